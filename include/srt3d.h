@@ -1,0 +1,212 @@
+/*
+ * srt3d.h - C ABI of the Sketched RT3D (SRT3D) hot path on one NVIDIA GB300
+ * (sm_103a). Library: libsrt3d.so (built in-tree by
+ * paper_2203_00952_gb300/build.py).
+ *
+ * Notation follows Tachella, Sheehan & Davies, "Sketched RT3D: How to
+ * reconstruct billions of photons per second" (ICASSP 2022):
+ *   x_p      photon time-of-arrival stamps, integers in [0, T-1]  (Sec. 2, Eq. 1)
+ *   T        number of time bins of the stamp range               (Sec. 2, Eq. 1)
+ *   y_b      per-pixel histogram, one bin per integer stamp       (Sec. 2, Eq. 2)
+ *   m        number of sketch entries                             (Sec. 2, Eq. 3)
+ *   z_l      sketch (1/n) sum_p exp(i w_l x_p), w_l = 2 pi l / T  (Sec. 2, Eq. 3)
+ *   h        impulse response, hhat its transform                 (Sec. 2, Eqs. 1, 4)
+ *   t_k, alpha_k, alpha_0   depths, signal and background probabilities
+ *   N_r x N_c pixel array (rows x cols), pixel p = r * cols + c   (Sec. 3)
+ *
+ * Conventions for every entry point
+ *   - Pointers marked "device" are CUDA device pointers on the context's
+ *     device; "host" pointers are ordinary host memory. The caller owns every
+ *     buffer it passes; the library owns only its internal scratch, its
+ *     lookup tables and (for serving) the frame slots.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Compute
+ *     entry points are asynchronous on that stream: they validate their
+ *     arguments, launch, and return. Argument errors return synchronously
+ *     and launch nothing.
+ *   - Errors detected by a kernel (a stamp >= T, a malformed offset array, a
+ *     histogram count above 65535) are latched in the context and returned by
+ *     the next srt3d_sync() on that stream. Kernels never trap: the offending
+ *     photon / pixel is skipped and the flag is set.
+ *   - There is no CPU fallback. Without a usable CUDA device srt3d_create()
+ *     returns SRT3D_ECUDA.
+ *   - A context may be used from one thread at a time for the compute entry
+ *     points; the serving entry points (srt3d_submit / srt3d_poll) are
+ *     internally locked and may be called from any thread.
+ *   - The first call with a new T (lookup tables) or a larger problem size
+ *     (scratch) allocates and synchronises; later calls with the same or
+ *     smaller sizes do not. Make such a first call before capturing a stream.
+ */
+#ifndef SRT3D_H
+#define SRT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int srt3d_status;
+
+enum {
+  SRT3D_OK = 0,
+  SRT3D_EINVAL = -1,    /* invalid argument (synchronous)                      */
+  SRT3D_ENOMEM = -2,    /* device or host allocation failed                    */
+  SRT3D_ERANGE = -3,    /* a stamp >= T or a count > 65535 was seen (latched)  */
+  SRT3D_ECUDA = -4,     /* CUDA runtime error; see srt3d_last_error()          */
+  SRT3D_EAGAIN = -5,    /* serving: result not ready yet                       */
+  SRT3D_ETIMEDOUT = -6, /* serving: poll timed out, or a device wait gave up   */
+  SRT3D_EBUSY = -7,     /* serving: frame not admitted now (HBM budget/slots)  */
+  SRT3D_ENOTFOUND = -8, /* serving: unknown frame id                           */
+  SRT3D_EOFFSETS = -9   /* malformed CSR offsets seen by a kernel (latched)    */
+};
+
+/* Arithmetic of the histogram sketch (srt3d_sketch_hist). */
+enum {
+  SRT3D_FP32 = 0,       /* FP32 CUDA-core product with exact integer phases    */
+  SRT3D_FP16_SPLIT = 1, /* tensor cores: FP16 counts x (F_hi + F_lo) FP16,
+                           FP32 accumulation in TMEM                           */
+  SRT3D_BF16 = 2        /* tensor cores: BF16 counts x BF16 F, FP32 accumulate */
+};
+
+/* Initialisation of srt3d_reconstruct. */
+enum {
+  SRT3D_INIT_MATCHED = 0, /* per-pixel sketched matched filter                 */
+  SRT3D_INIT_GIVEN = 1    /* start from the depth/alpha/active passed in       */
+};
+
+typedef struct srt3d_ctx srt3d_ctx;
+
+/* Reconstruction parameters (Sec. 3; the RT3D iteration the paper cites).
+ * Field order and types are part of the ABI. */
+typedef struct srt3d_params {
+  uint32_t iters;      /* SRT3D iterations after initialisation              */
+  uint32_t k_max;      /* surfaces per pixel, 1 or 2                         */
+  uint32_t radius;     /* APSS pixel window half-width, 1..3                 */
+  int32_t init_mode;   /* SRT3D_INIT_MATCHED or SRT3D_INIT_GIVEN             */
+  int32_t regularize;  /* 1: SRT3D (APSS + intensity smoothing);
+                          0: pixelwise sketched estimate (no spatial prior)  */
+  float apss_h;        /* APSS weight support, pixel pitches                 */
+  float d_max;         /* neighbour depth gate and largest APSS move, bins   */
+  float depth_scale;   /* pixel pitches per time bin in point coordinates    */
+  float prune_alpha;   /* a point with alpha below this is removed           */
+  float smooth_lambda; /* intensity smoothing weight in [0, 1]               */
+  float min_sep;       /* init: least circular separation of 2 surfaces, bins */
+} srt3d_params;
+
+/* Create a context on CUDA device `device`. hbm_budget_bytes bounds the device
+ * memory the serving runtime may hold for admitted frames (0 = 3/4 of the
+ * free memory at creation). *out receives the context. */
+srt3d_status srt3d_create(int device, size_t hbm_budget_bytes, srt3d_ctx** out);
+
+/* Destroy a context: waits for its work, frees its scratch, tables and slots. */
+void srt3d_destroy(srt3d_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* srt3d_status_string(srt3d_status status);
+
+/* Message of the last error raised on this context (owned by the context,
+ * valid until the next call on it). */
+const char* srt3d_last_error(srt3d_ctx* ctx);
+
+/* Synchronise `stream` and report errors latched by kernels since the last
+ * srt3d_sync on this context: SRT3D_ERANGE (stamp >= T or count > 65535),
+ * SRT3D_EOFFSETS (offsets not non-decreasing or beyond num_stamps), or
+ * SRT3D_ECUDA. Clears the latched flags. */
+srt3d_status srt3d_sync(srt3d_ctx* ctx, void* stream);
+
+/* Per-pixel histogram of a pixel-sorted stamp stream (Sec. 2, Eq. 2 with
+ * T' = T and unit bins: y_b = #{p : x_p = b}).
+ *   stamps   device, uint16 [num_stamps], pixel-sorted (any 2-byte alignment)
+ *   offsets  device, uint32 [num_pixels + 1], CSR: the photons of pixel p are
+ *            stamps[offsets[p] .. offsets[p+1]); offsets[num_pixels] <= num_stamps
+ *   T        1..65536
+ *   hist     device, uint16 [num_pixels][T] row-major, overwritten
+ * Counts above 65535 saturate and latch SRT3D_ERANGE. */
+srt3d_status srt3d_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                    uint64_t num_stamps, uint32_t num_pixels, uint32_t T,
+                                    uint16_t* hist, void* stream);
+
+/* Photon sketch of a pixel-sorted stamp stream (Sec. 2, Eq. 3, unnormalised):
+ *   S[p][l-1] = sum over the photons of pixel p of exp(i 2 pi k / T),
+ *   k = (l * x_p) mod T computed exactly in integers, l = 1..m;  n[p] = count.
+ *   stamps, offsets, num_stamps, T as for srt3d_hist_from_stream
+ *   m        1..32
+ *   accumulate  0: overwrite S and n;  1: add into S and n (online update of
+ *            Sec. 2: a frame's photons may arrive in chunks)
+ *   S        device, float [num_pixels][m][2] (re, im interleaved)
+ *   n        device, uint32 [num_pixels]
+ * Stamps >= T are skipped and latch SRT3D_ERANGE. */
+srt3d_status srt3d_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                 uint64_t num_stamps, uint32_t num_pixels, uint32_t T, uint32_t m,
+                                 int accumulate, float* S, uint32_t* n, void* stream);
+
+/* Sketch of histograms (Sec. 2, Eqs. 2-3): S[p][l-1] = sum_b y[p][b] exp(i 2 pi
+ * ((l b) mod T) / T), n[p] = sum_b y[p][b], as the product Y[P x T] F[T x 2m].
+ *   hist      device, uint16 [num_pixels][T] row-major; 16-byte aligned base
+ *             for the tensor-core precisions
+ *   T         1..65536 (tensor-core precisions: a multiple of 64)
+ *   m         1..32
+ *   precision SRT3D_FP32, SRT3D_FP16_SPLIT or SRT3D_BF16
+ *   S, n      as for srt3d_sketch_stream (overwritten) */
+srt3d_status srt3d_sketch_hist(srt3d_ctx* ctx, const uint16_t* hist, uint32_t num_pixels, uint32_t T,
+                               uint32_t m, int precision, float* S, uint32_t* n, void* stream);
+
+/* Normalise sketch states (Sec. 2, Eq. 3): z = S / n, and z = 0 where n = 0.
+ *   S  device float [P][m][2];  n device uint32 [P];  z device float [P][m][2]
+ *   (z may alias S). */
+srt3d_status srt3d_finalize(srt3d_ctx* ctx, const float* S, const uint32_t* n, uint32_t num_pixels,
+                            uint32_t m, float* z, void* stream);
+
+/* SRT3D reconstruction from sketches (Sec. 3, Eq. 8 with W = I): initialise
+ * (matched filter or given), then params->iters iterations of: sketched
+ * gradient step on every point, APSS depth projection and intensity
+ * smoothing / pruning over pixel-grid neighbourhoods (the RT3D iteration that
+ * Sec. 3 adopts).
+ *   z         device float [P][m][2], normalised sketches (srt3d_finalize)
+ *   n         device uint32 [P] photon counts, P = rows * cols
+ *   rows, cols  array size N_r x N_c, pixel p = r * cols + c
+ *   T, m      time bins (2..65536) and sketch size (1..32)
+ *   h         device float [T], impulse response by circular lag (peak at 0)
+ *   params    host, see srt3d_params
+ *   depth     device float [P][k_max], bins in [0, T)      (in/out)
+ *   alpha     device float [P][k_max], probabilities        (in/out)
+ *   active    device uint8 [P][k_max], 1 = point present    (in/out)
+ *   alpha0    device float [P], background probability      (out)
+ * With SRT3D_INIT_GIVEN depth/alpha/active are read as the initial state. */
+srt3d_status srt3d_reconstruct(srt3d_ctx* ctx, const float* z, const uint32_t* n, uint32_t rows,
+                               uint32_t cols, uint32_t T, uint32_t m, const float* h,
+                               const srt3d_params* params, float* depth, float* alpha,
+                               uint8_t* active, float* alpha0, void* stream);
+
+/* Serving (continuous batching). A frame is opened by its first chunk,
+ * receives photon chunks as host CSR arrays that are sketched online into a
+ * device-resident per-pixel state, and is reconstructed after its last chunk.
+ * Frames are admitted while their device state fits the context's HBM budget
+ * and a slot is free; chunks of admitted frames and reconstructions of
+ * different frames overlap on the device.
+ *   frame_id   caller-chosen id, unique among frames in flight
+ *   rows, cols, T, m, params  as for srt3d_reconstruct (read on the first chunk)
+ *   h          host float [T] (read on the first chunk)
+ *   chunk_stamps   host uint16 [chunk_offsets[rows*cols]], pixel-sorted
+ *   chunk_offsets  host uint32 [rows*cols + 1]
+ *   last_chunk 1 on the frame's final chunk
+ * Returns SRT3D_EBUSY (nothing consumed; retry later) when the frame cannot
+ * be admitted yet. The host arrays are copied before return. */
+srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t rows, uint32_t cols, uint32_t T,
+                          uint32_t m, const float* h, const srt3d_params* params,
+                          const uint16_t* chunk_stamps, const uint32_t* chunk_offsets, int last_chunk);
+
+/* Wait up to timeout_us for frame_id's result and copy it to host buffers
+ * depth/alpha [P][k_max] float, active [P][k_max] uint8, alpha0 [P] float and
+ * (if not NULL) n [P] uint32. Returns SRT3D_OK and releases the frame,
+ * SRT3D_ETIMEDOUT if not done in time, SRT3D_ENOTFOUND for an unknown id, or
+ * the frame's error status. */
+srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t timeout_us, float* depth,
+                        float* alpha, uint8_t* active, float* alpha0, uint32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRT3D_H */

@@ -1,0 +1,32 @@
+// Device helpers shared by the kernels of libsrt3d.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace srt3d {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// (j * x) mod T, exact for j * x < 2^24: the product is exact in float, the
+// float quotient is within 1 of floor(j x / T), and one correction fixes it.
+__device__ __forceinline__ uint32_t mulmod(uint32_t j, uint32_t x, uint32_t T, float invT) {
+  const uint32_t a = j * x;
+  const uint32_t q = __float2uint_rz(__uint2float_rn(a) * invT);
+  int32_t r = int32_t(a) - int32_t(q * T);
+  r += (r < 0) ? int32_t(T) : 0;
+  r -= (r >= int32_t(T)) ? int32_t(T) : 0;
+  return uint32_t(r);
+}
+
+// e^{i 2 pi k / T} from the phase table in shared memory (direct, or
+// two-level lo[256] x hi[ceil(T/256)]).
+__device__ __forceinline__ float2 phase(const float2* tab, uint32_t k, bool two_level) {
+  if (!two_level) return tab[k];
+  return cmul(tab[k & 255u], tab[256u + (k >> 8)]);
+}
+
+}  // namespace srt3d

@@ -1,0 +1,96 @@
+// Internal declarations shared by the translation units of libsrt3d.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/srt3d.h"
+
+namespace srt3d {
+
+// Bits of the device error word latched by kernels.
+enum : uint32_t {
+  FLAG_STAMP_RANGE = 1u,   // a stamp >= T
+  FLAG_OFFSETS = 2u,       // offsets decreasing or beyond num_stamps
+  FLAG_COUNT_RANGE = 4u,   // a histogram count > 65535
+  FLAG_DEVICE_TIMEOUT = 8u // a bounded device wait gave up
+};
+
+// Phase table for one T: cos/sin of 2 pi k / T, k in [0, T), computed on the
+// host in double and rounded to float. For T <= kDirectTableMax the table is
+// direct (T entries); above it is two-level: lo[256] = e^{i 2 pi k_lo / T},
+// hi[ceil(T/256)] = e^{i 2 pi 256 k_hi / T}, k = 256 k_hi + k_lo.
+constexpr uint32_t kDirectTableMax = 8192;
+struct PhaseTable {
+  float2* dev = nullptr;
+  uint32_t entries = 0;
+  bool two_level = false;
+};
+
+// Growable device buffer owned by the context.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Serving;  // serving runtime (serve.cu)
+
+}  // namespace srt3d
+
+struct srt3d_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  size_t hbm_budget = 0;
+  std::string last_error;
+  uint32_t* d_flags = nullptr;  // device error word
+  std::map<uint32_t, srt3d::PhaseTable> tables;
+  // reconstruction scratch
+  srt3d::DevBuf rc_scratch;
+  // histogram tensor-core operands keyed by (T, m, precision)
+  std::map<std::tuple<uint32_t, uint32_t, int>, srt3d::DevBuf> fourier;
+  std::mutex mu;  // guards tables/scratch growth for concurrent serving streams
+  srt3d::Serving* serving = nullptr;
+  // autotuned launch shapes: key -> value
+  std::map<uint64_t, int> tuned;
+};
+
+namespace srt3d {
+
+srt3d_status set_error(srt3d_ctx* ctx, srt3d_status st, const std::string& msg);
+srt3d_status cuda_error(srt3d_ctx* ctx, cudaError_t err, const char* what);
+srt3d_status get_phase_table(srt3d_ctx* ctx, uint32_t T, PhaseTable* out);
+srt3d_status grow(srt3d_ctx* ctx, DevBuf* buf, size_t bytes);
+
+// Launchers (no argument validation; callers validate).
+srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                  uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m,
+                                  int accumulate, float2* S, uint32_t* n, cudaStream_t stream);
+srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n, uint32_t P,
+                             uint32_t m, float2* z, cudaStream_t stream);
+srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                     uint64_t num_stamps, uint32_t P, uint32_t T, uint16_t* hist,
+                                     cudaStream_t stream);
+srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows,
+                              uint32_t cols, uint32_t T, uint32_t m, const float* h,
+                              const srt3d_params& prm, float* depth, float* alpha, uint8_t* active,
+                              float* alpha0, void* scratch, size_t scratch_bytes, cudaStream_t stream);
+size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m);
+srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint32_t T, uint32_t m,
+                             const srt3d_params* prm);
+
+void serving_destroy(srt3d_ctx* ctx);
+
+}  // namespace srt3d
+
+#define SRT3D_CUDA_TRY(ctx, expr)                                  \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) return ::srt3d::cuda_error(ctx, _e, #expr); \
+  } while (0)

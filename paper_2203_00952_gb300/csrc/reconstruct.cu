@@ -1,0 +1,628 @@
+// SRT3D reconstruction from sketches (Sec. 3, Eq. 8 with W = I).
+//
+// The paper replaces RT3D's histogram likelihood by the sketched loss
+// n ||z - Psi_theta||^2 (Eq. 6) and keeps RT3D's point-cloud prior; the
+// iteration implemented here (one reading of the cited RT3D) is, per pixel p
+// with up to K = 2 points (t_k, alpha_k):
+//   k_prep    hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau} (Eq. 4), the global
+//             step sizes, and n_max
+//   k_init    sketched matched filter: argmax over integer t of
+//             Re sum_l conj(hhat_l e^{i w_l t}) z_l (Horner in w = e^{-i 2pi t/T}),
+//             alpha = s / sum|hhat|^2, second surface from the residual
+//   per iteration:
+//   k_grad    Jacobi gradient step on n ||z - Psi||^2 (t, alpha), alpha >= 0,
+//             sum alpha <= 1
+//   k_normals weighted least-squares plane over the (2r+1)^2 x K neighbours
+//             gated by |dt| <= d_max and the APSS weight (1 - d^2/h^2)^4
+//   k_sphere  algebraic sphere fit with normals (Guennebaud & Gross 2007)
+//             and projection along the line of sight; intensity smoothing,
+//             pruning, alpha_0 = 1 - sum alpha
+// The iteration state lives in the caller's depth/alpha/active buffers; the
+// post-gradient state, normals, hhat and step sizes live in a scratch block.
+#include <cfloat>
+#include <cmath>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace srt3d {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kMaxM = 32;
+
+// misc[] slots in the scratch block
+enum { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_COUNT = 8 };
+
+struct Scratch {
+  float* t1;
+  float* a1;
+  float4* nrm;
+  uint8_t* act1;
+  float2* hh;
+  float* misc;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Scratch carve(void* base, uint32_t P, uint32_t K) {
+  char* p = static_cast<char*>(base);
+  Scratch s;
+  const size_t pk = size_t(P) * K;
+  s.nrm = reinterpret_cast<float4*>(p);
+  p += align256(pk * sizeof(float4));
+  s.t1 = reinterpret_cast<float*>(p);
+  p += align256(pk * sizeof(float));
+  s.a1 = reinterpret_cast<float*>(p);
+  p += align256(pk * sizeof(float));
+  s.act1 = reinterpret_cast<uint8_t*>(p);
+  p += align256(pk);
+  s.hh = reinterpret_cast<float2*>(p);
+  p += align256(kMaxM * sizeof(float2));
+  s.misc = reinterpret_cast<float*>(p);
+  return s;
+}
+
+__device__ __forceinline__ void load_table(float2* s_tab, const float2* table, uint32_t entries) {
+  for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_tab[i] = table[i];
+  __syncthreads();
+}
+
+// One block: hhat (FP32 partial sums per thread, then a tree), H, n_max, and
+// the step-size bases eta_t * n_max, eta_alpha * n_max.
+__global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
+                                               uint32_t P, uint32_t T, uint32_t m, uint32_t K,
+                                               const float2* __restrict__ table, uint32_t entries, int two_level,
+                                               float2* __restrict__ hh_out, float* __restrict__ misc) {
+  extern __shared__ float2 s_tab[];
+  __shared__ float s_red[2][32];
+  __shared__ float s_H;
+  __shared__ uint32_t s_nmax;
+  load_table(s_tab, table, entries);
+  const bool tl = two_level != 0;
+  const float invT = 1.0f / float(T);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_nmax = 0u;
+  // H = sum h
+  float hs = 0.f;
+  for (uint32_t tau = threadIdx.x; tau < T; tau += blockDim.x) hs += h[tau];
+  for (int off = 16; off; off >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, off);
+  if (lane == 0) s_red[0][warp] = hs;
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < nw ? s_red[0][lane] : 0.f;
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) s_H = v;
+  }
+  __syncthreads();
+  for (uint32_t l = 1; l <= m; ++l) {
+    float re = 0.f, im = 0.f;
+    for (uint32_t tau = threadIdx.x; tau < T; tau += blockDim.x) {
+      const float2 e = phase(s_tab, mulmod(l, tau, T, invT), tl);
+      const float hv = h[tau];
+      re = fmaf(hv, e.x, re);
+      im = fmaf(hv, e.y, im);
+    }
+    for (int off = 16; off; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    __syncthreads();
+    if (lane == 0) {
+      s_red[0][warp] = re;
+      s_red[1][warp] = im;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      float vr = lane < nw ? s_red[0][lane] : 0.f;
+      float vi = lane < nw ? s_red[1][lane] : 0.f;
+      for (int off = 16; off; off >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, off);
+        vi += __shfl_xor_sync(0xffffffffu, vi, off);
+      }
+      if (lane == 0) hh_out[l - 1] = make_float2(vr / s_H, vi / s_H);
+    }
+  }
+  uint32_t nm = 0u;
+  for (uint32_t p = threadIdx.x; p < P; p += blockDim.x) nm = max(nm, n[p]);
+  for (int off = 16; off; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
+  if (lane == 0) atomicMax(&s_nmax, nm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sw = 0.f, sa = 0.f;
+    for (uint32_t l = 1; l <= m; ++l) {
+      const float2 v = hh_out[l - 1];
+      const float a = sqrtf(v.x * v.x + v.y * v.y);
+      const float w = 6.283185307179586f * float(l) / float(T);
+      sw += w * w * a * (a + 2.f);
+      sa += a * a;
+    }
+    misc[MISC_ETA_T] = 1.f / (2.f * sw);
+    misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
+    misc[MISC_E2] = sa;
+    misc[MISC_NMAX] = float(max(s_nmax, 1u));
+  }
+}
+
+// Horner evaluation of Re sum_{l=1}^{m} c_l w^l, w = e^{-i 2 pi t / T}; one
+// lane per t, best (score, smallest t) per warp.
+__device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, uint32_t T, const float2* s_tab,
+                                                   bool tl, int excl_t, float min_sep, float* best_s,
+                                                   uint32_t* best_t) {
+  const uint32_t lane = threadIdx.x & 31u;
+  float bs = -FLT_MAX;
+  uint32_t bt = 0xffffffffu;
+  for (uint32_t t = lane; t < T; t += 32u) {
+    if (excl_t >= 0) {
+      const uint32_t d0 = t > uint32_t(excl_t) ? t - uint32_t(excl_t) : uint32_t(excl_t) - t;
+      const uint32_t d = min(d0, T - d0);
+      if (float(d) < min_sep) continue;
+    }
+    float2 w = phase(s_tab, t, tl);
+    w.y = -w.y;
+    float ax = c[m - 1].x, ay = c[m - 1].y;
+    for (int l = int(m) - 2; l >= 0; --l) {
+      const float nx = fmaf(ax, w.x, fmaf(-ay, w.y, c[l].x));
+      const float ny = fmaf(ax, w.y, fmaf(ay, w.x, c[l].y));
+      ax = nx;
+      ay = ny;
+    }
+    const float s = fmaf(ax, w.x, -ay * w.y);
+    if (s > bs) {
+      bs = s;
+      bt = t;
+    }
+  }
+  for (int off = 16; off; off >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, bs, off);
+    const uint32_t ot = __shfl_xor_sync(0xffffffffu, bt, off);
+    if (os > bs || (os == bs && ot < bt)) {
+      bs = os;
+      bt = ot;
+    }
+  }
+  *best_s = bs;
+  *best_t = bt;
+}
+
+// Matched-filter initialisation, one warp per pixel.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
+                                                 uint32_t P, uint32_t T, uint32_t m,
+                                                 const float2* __restrict__ table, uint32_t entries,
+                                                 int two_level, const float2* __restrict__ hh_g,
+                                                 const float* __restrict__ misc, float prune_alpha, float min_sep,
+                                                 float* __restrict__ depth, float* __restrict__ alpha,
+                                                 uint8_t* __restrict__ active, float* __restrict__ alpha0) {
+  extern __shared__ float2 s_tab[];
+  __shared__ float2 s_c[kBlock / 32][kMaxM];
+  __shared__ float2 s_hh[kMaxM];
+  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
+  load_table(s_tab, table, entries);
+  const bool tl = two_level != 0;
+  const float invT = 1.0f / float(T);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  const float E2 = misc[MISC_E2];
+  float2* c = s_c[warp];
+  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb) {
+    const uint32_t cnt = n[p];
+    if (lane < m) {
+      const float2 zl = z[size_t(p) * m + lane];
+      const float2 hc = make_float2(s_hh[lane].x, -s_hh[lane].y);
+      c[lane] = cmul(hc, zl);
+    }
+    __syncwarp();
+    float s1;
+    uint32_t t1;
+    warp_argmax_scores(c, m, T, s_tab, tl, -1, 0.f, &s1, &t1);
+    if (t1 >= T) {  // no finite score (cannot happen for finite z)
+      t1 = 0u;
+      s1 = 0.f;
+    }
+    float a[K], t[K];
+    bool act[K];
+    a[0] = fmaxf(0.f, s1 / E2);
+    t[0] = float(t1);
+    act[0] = (a[0] >= prune_alpha) && cnt > 0;
+    if (K == 2) {
+      __syncwarp();
+      if (lane < m) {
+        const float2 zl = z[size_t(p) * m + lane];
+        const float2 hv = s_hh[lane];
+        const float2 e = phase(s_tab, mulmod(lane + 1u, t1, T, invT), tl);
+        const float f = (a[0] >= prune_alpha) ? a[0] : 0.f;
+        const float2 fit = cmul(hv, e);
+        const float2 r = make_float2(zl.x - f * fit.x, zl.y - f * fit.y);
+        c[lane] = cmul(make_float2(hv.x, -hv.y), r);
+      }
+      __syncwarp();
+      float s2;
+      uint32_t t2;
+      warp_argmax_scores(c, m, T, s_tab, tl, int(t1), min_sep, &s2, &t2);
+      if (t2 >= T) {
+        t2 = 0u;
+        s2 = 0.f;
+      }
+      a[K - 1] = fmaxf(0.f, s2 / E2);
+      t[K - 1] = float(t2);
+      act[K - 1] = (a[K - 1] >= prune_alpha) && cnt > 0;
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (!act[k]) a[k] = 0.f;
+      sum += a[k];
+    }
+    if (sum > 1.f) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
+      sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) sum += a[k];
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        depth[size_t(p) * K + k] = t[k];
+        alpha[size_t(p) * K + k] = a[k];
+        active[size_t(p) * K + k] = act[k] ? 1 : 0;
+      }
+      alpha0[p] = 1.f - sum;
+    }
+    __syncwarp();
+  }
+}
+
+// Sketched gradient step (Jacobi), one thread per pixel. With `direct` the
+// result is the new state (pixelwise mode); otherwise it goes to scratch for
+// the denoisers.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, const uint32_t* __restrict__ n,
+                                                 uint32_t P, uint32_t T, uint32_t m,
+                                                 const float2* __restrict__ hh_g, const float* __restrict__ misc,
+                                                 const float* depth, const float* alpha, const uint8_t* active,
+                                                 float* t_out, float* a_out, uint8_t* act_out, float* alpha0_out) {
+  __shared__ float2 s_hh[kMaxM];
+  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
+  __syncthreads();
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float Tf = float(T);
+  const float nmax = misc[MISC_NMAX];
+  const float eta_t = misc[MISC_ETA_T] / nmax;
+  const float eta_a = misc[MISC_ETA_A] / nmax;
+  float t[K], a[K];
+  bool act[K];
+  float2 e1[K], E[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    t[k] = depth[size_t(p) * K + k];
+    a[k] = alpha[size_t(p) * K + k];
+    act[k] = active[size_t(p) * K + k] != 0;
+    float sn, cs;
+    sincospif(2.f * t[k] / Tf, &sn, &cs);
+    e1[k] = make_float2(cs, sn);
+    E[k] = e1[k];
+  }
+  float gt[K], ga[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) gt[k] = ga[k] = 0.f;
+  const float wstep = 6.283185307179586f / Tf;
+  const float2* zp = z + size_t(p) * m;
+  for (uint32_t l = 0; l < m; ++l) {
+    const float2 hv = s_hh[l];
+    const float2 zl = zp[l];
+    float2 q[K];
+    float2 psi = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      q[k] = cmul(hv, E[k]);
+      if (act[k]) {
+        psi.x = fmaf(a[k], q[k].x, psi.x);
+        psi.y = fmaf(a[k], q[k].y, psi.y);
+      }
+    }
+    const float2 r = make_float2(zl.x - psi.x, zl.y - psi.y);
+    const float w = wstep * float(l + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      ga[k] += r.x * q[k].x + r.y * q[k].y;
+      gt[k] += w * a[k] * (r.y * q[k].x - r.x * q[k].y);
+      E[k] = cmul(E[k], e1[k]);
+    }
+  }
+  const float nn = -2.f * float(n[p]);
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (act[k]) {
+      float x = t[k] - eta_t * (nn * gt[k]);
+      x -= floorf(x / Tf) * Tf;
+      if (x >= Tf) x -= Tf;
+      if (x < 0.f) x += Tf;
+      t[k] = x;
+      a[k] = fmaxf(a[k] - eta_a * (nn * ga[k]), 0.f);
+    } else {
+      a[k] = 0.f;
+    }
+    sum += a[k];
+  }
+  if (sum > 1.f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
+  }
+  float s2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    t_out[size_t(p) * K + k] = t[k];
+    a_out[size_t(p) * K + k] = a[k];
+    s2 += a[k];
+    if (act_out) act_out[size_t(p) * K + k] = act[k] ? 1 : 0;
+  }
+  if (alpha0_out) alpha0_out[p] = 1.f - s2;
+}
+
+struct Stencil {
+  uint32_t rows, cols, radius;
+  float h2, inv_h2, d_max, ds;
+};
+
+// Neighbour visitor shared by the two denoiser kernels: calls f(dx, dy, dz, w, q, k2)
+// for every active neighbour point with positive APSS weight (query included).
+template <int K, typename F>
+__device__ __forceinline__ void for_neighbours(const Stencil st, uint32_t r0, uint32_t c0, float tq,
+                                               const float* __restrict__ t1, const uint8_t* __restrict__ act1,
+                                               F&& f) {
+  const int R = int(st.radius);
+  for (int dr = -R; dr <= R; ++dr) {
+    const int rr = int(r0) + dr;
+    if (rr < 0 || rr >= int(st.rows)) continue;
+    for (int dc = -R; dc <= R; ++dc) {
+      const int cc = int(c0) + dc;
+      if (cc < 0 || cc >= int(st.cols)) continue;
+      const uint32_t q = uint32_t(rr) * st.cols + uint32_t(cc);
+#pragma unroll
+      for (int k2 = 0; k2 < K; ++k2) {
+        if (!act1[size_t(q) * K + k2]) continue;
+        const float dt = t1[size_t(q) * K + k2] - tq;
+        if (fabsf(dt) > st.d_max) continue;
+        const float dz = dt * st.ds;
+        const float fx = float(dc), fy = float(dr);
+        const float d2 = fx * fx + fy * fy + dz * dz;
+        if (d2 >= st.h2) continue;
+        const float u = 1.f - d2 * st.inv_h2;
+        const float u2 = u * u;
+        f(fx, fy, dz, u2 * u2, q, k2);
+      }
+    }
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock, 4) k_normals(Stencil st, const float* __restrict__ t1,
+                                                    const uint8_t* __restrict__ act1, float4* __restrict__ nrm) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= st.rows * st.cols) return;
+  const uint32_t r0 = p / st.cols, c0 = p - r0 * st.cols;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float4 out = make_float4(0.f, 0.f, 1.f, 0.f);
+    if (act1[size_t(p) * K + k]) {
+      const float tq = t1[size_t(p) * K + k];
+      float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
+      int cnt = 0;
+      for_neighbours<K>(st, r0, c0, tq, t1, act1, [&](float x, float y, float zz, float w, uint32_t, int) {
+        Sw += w;
+        Sx += w * x;
+        Sy += w * y;
+        Sz += w * zz;
+        Sxx += w * x * x;
+        Sxy += w * x * y;
+        Syy += w * y * y;
+        Sxz += w * x * zz;
+        Syz += w * y * zz;
+        ++cnt;
+      });
+      const float det = Sw * (Sxx * Syy - Sxy * Sxy) - Sx * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Sxy - Sxx * Sy);
+      if (cnt >= 3 && det > 1e-6f * Sw * Sw * Sw) {
+        const float db = Sw * (Sxz * Syy - Sxy * Syz) - Sz * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Syz - Sxz * Sy);
+        const float dcf = Sw * (Sxx * Syz - Sxz * Sxy) - Sx * (Sx * Syz - Sxz * Sy) + Sz * (Sx * Sxy - Sxx * Sy);
+        const float b = db / det, c = dcf / det;
+        const float inv = 1.f / sqrtf(b * b + c * c + 1.f);
+        out = make_float4(-b * inv, -c * inv, inv, 0.f);
+      }
+    }
+    nrm[size_t(p) * K + k] = out;
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_sphere(Stencil st, float lambda, float prune_alpha,
+                                                   const float* __restrict__ t1, const float* __restrict__ a1,
+                                                   const uint8_t* __restrict__ act1, const float4* __restrict__ nrm,
+                                                   float* __restrict__ depth, float* __restrict__ alpha,
+                                                   uint8_t* __restrict__ active, float* __restrict__ alpha0) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= st.rows * st.cols) return;
+  const uint32_t r0 = p / st.cols, c0 = p - r0 * st.cols;
+  float tout[K], aout[K];
+  bool aact[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float tq = t1[size_t(p) * K + k];
+    tout[k] = tq;
+    aout[k] = 0.f;
+    aact[k] = false;
+    if (!act1[size_t(p) * K + k]) continue;
+    float Sw = 0, Spx = 0, Spy = 0, Spz = 0, Snx = 0, Sny = 0, Snz = 0, Spn = 0, Spp = 0, Swa = 0;
+    int cnt = 0;
+    for_neighbours<K>(st, r0, c0, tq, t1, act1, [&](float x, float y, float zz, float w, uint32_t q, int k2) {
+      const float4 nv = nrm[size_t(q) * K + k2];
+      Sw += w;
+      Spx += w * x;
+      Spy += w * y;
+      Spz += w * zz;
+      Snx += w * nv.x;
+      Sny += w * nv.y;
+      Snz += w * nv.z;
+      Spn += w * (x * nv.x + y * nv.y + zz * nv.z);
+      Spp += w * (x * x + y * y + zz * zz);
+      Swa += w * a1[size_t(q) * K + k2];
+      ++cnt;
+    });
+    const float den = Spp - (Spx * Spx + Spy * Spy + Spz * Spz) / Sw;
+    if (cnt >= 3 && den > 0.f) {
+      const float u4 = 0.5f * (Spn - (Spx * Snx + Spy * Sny + Spz * Snz) / Sw) / den;
+      const float ux = (Snx - 2.f * u4 * Spx) / Sw;
+      const float uy = (Sny - 2.f * u4 * Spy) / Sw;
+      const float uz = (Snz - 2.f * u4 * Spz) / Sw;
+      const float u0 = -(ux * Spx + uy * Spy + uz * Spz + u4 * Spp) / Sw;
+      const float disc = uz * uz - 4.f * u4 * u0;
+      if (disc >= 0.f) {
+        const float sq = sqrtf(disc);
+        const float qq = -0.5f * (uz + (uz >= 0.f ? sq : -sq));
+        if (qq != 0.f) {
+          const float zn = u0 / qq;
+          const float zf = (u4 != 0.f) ? qq / u4 : INFINITY;
+          const float zs = (fabsf(zf) < fabsf(zn)) ? zf : zn;
+          if (fabsf(zs) <= st.d_max * st.ds) tout[k] = tq + zs / st.ds;
+        }
+      }
+    }
+    const float aq = a1[size_t(p) * K + k];
+    const float an = (1.f - lambda) * aq + lambda * (Swa / Sw);
+    aact[k] = an >= prune_alpha;
+    aout[k] = aact[k] ? an : 0.f;
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) sum += aout[k];
+  if (sum > 1.f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) aout[k] = aout[k] / sum;
+    sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sum += aout[k];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    depth[size_t(p) * K + k] = tout[k];
+    alpha[size_t(p) * K + k] = aout[k];
+    active[size_t(p) * K + k] = aact[k] ? 1 : 0;
+  }
+  alpha0[p] = 1.f - sum;
+}
+
+template <int K>
+__global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint8_t* __restrict__ active,
+                         float* __restrict__ alpha0) {
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) s += active[size_t(p) * K + k] ? alpha[size_t(p) * K + k] : 0.f;
+  alpha0[p] = 1.f - s;
+}
+
+template <int K>
+srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows, uint32_t cols, uint32_t T,
+                 uint32_t m, const float* h, const srt3d_params& prm, float* depth, float* alpha, uint8_t* active,
+                 float* alpha0, const Scratch& sc, const PhaseTable& tab, cudaStream_t stream) {
+  const uint32_t P = rows * cols;
+  const size_t tab_smem = size_t(tab.entries) * sizeof(float2);
+  const int tl = tab.two_level ? 1 : 0;
+  if (tab_smem > 48 * 1024) {
+    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+  }
+  k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  if (prm.init_mode == SRT3D_INIT_MATCHED) {
+    int bps = 0;
+    SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init<K>, kBlock, tab_smem));
+    if (bps < 1) bps = 1;
+    const uint32_t wpb = kBlock / 32;
+    const uint64_t need = (uint64_t(P) + wpb - 1) / wpb;
+    const uint32_t grid = uint32_t(std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps));
+    k_init<K><<<grid, kBlock, tab_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, sc.hh, sc.misc,
+                                                  prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
+    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  } else {
+    k_alpha0<K><<<(P + kBlock - 1) / kBlock, kBlock, 0, stream>>>(P, alpha, active, alpha0);
+    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  const uint32_t grid = (P + kBlock - 1) / kBlock;
+  Stencil st;
+  st.rows = rows;
+  st.cols = cols;
+  st.radius = prm.radius;
+  st.h2 = prm.apss_h * prm.apss_h;
+  st.inv_h2 = 1.f / st.h2;
+  st.d_max = prm.d_max;
+  st.ds = prm.depth_scale;
+  for (uint32_t it = 0; it < prm.iters; ++it) {
+    if (!prm.regularize) {
+      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, depth, alpha,
+                                             nullptr, alpha0);
+      SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+      continue;
+    }
+    k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, sc.t1, sc.a1,
+                                           sc.act1, nullptr);
+    k_normals<K><<<grid, kBlock, 0, stream>>>(st, sc.t1, sc.act1, sc.nrm);
+    k_sphere<K><<<grid, kBlock, 0, stream>>>(st, prm.smooth_lambda, prm.prune_alpha, sc.t1, sc.a1, sc.act1, sc.nrm,
+                                             depth, alpha, active, alpha0);
+    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return SRT3D_OK;
+}
+
+}  // namespace
+
+size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
+  (void)m;
+  const size_t pk = size_t(P) * k_max;
+  return align256(pk * sizeof(float4)) + 2 * align256(pk * sizeof(float)) + align256(pk) +
+         align256(kMaxM * sizeof(float2)) + align256(MISC_COUNT * sizeof(float));
+}
+
+srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows, uint32_t cols,
+                              uint32_t T, uint32_t m, const float* h, const srt3d_params& prm, float* depth,
+                              float* alpha, uint8_t* active, float* alpha0, void* scratch, size_t scratch_bytes,
+                              cudaStream_t stream) {
+  const uint32_t P = rows * cols;
+  if (scratch_bytes < reconstruct_scratch_bytes(P, prm.k_max, m))
+    return set_error(ctx, SRT3D_EINVAL, "reconstruction scratch too small");
+  PhaseTable tab;
+  srt3d_status st = get_phase_table(ctx, T, &tab);
+  if (st != SRT3D_OK) return st;
+  const Scratch sc = carve(scratch, P, prm.k_max);
+  if (prm.k_max == 1) return run<1>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+  return run<2>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+}
+
+}  // namespace srt3d
+
+using namespace srt3d;
+
+extern "C" srt3d_status srt3d_reconstruct(srt3d_ctx* ctx, const float* z, const uint32_t* n, uint32_t rows,
+                                          uint32_t cols, uint32_t T, uint32_t m, const float* h,
+                                          const srt3d_params* params, float* depth, float* alpha, uint8_t* active,
+                                          float* alpha0, void* stream) {
+  if (!ctx) return SRT3D_EINVAL;
+  srt3d_status st = validate_params(ctx, rows, cols, T, m, params);
+  if (st != SRT3D_OK) return st;
+  if (!z || !n || !h || !depth || !alpha || !active || !alpha0) return set_error(ctx, SRT3D_EINVAL, "NULL pointer");
+  if (reinterpret_cast<uintptr_t>(z) % 8) return set_error(ctx, SRT3D_EINVAL, "z must be 8-byte aligned");
+  const uint32_t P = rows * cols;
+  const size_t need = reconstruct_scratch_bytes(P, params->k_max, m);
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    st = grow(ctx, &ctx->rc_scratch, need);
+  }
+  if (st != SRT3D_OK) return st;
+  return reconstruct_impl(ctx, reinterpret_cast<const float2*>(z), n, rows, cols, T, m, h, *params, depth, alpha,
+                          active, alpha0, ctx->rc_scratch.ptr, ctx->rc_scratch.bytes,
+                          static_cast<cudaStream_t>(stream));
+}
