@@ -205,6 +205,17 @@ srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t rows, uint
 srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t timeout_us, float* depth,
                         float* alpha, uint8_t* active, float* alpha0, uint32_t* n);
 
+/* Measurement aid (the paper has no counterpart). With profiling enabled the
+ * library brackets each of its kernel launches with CUDA events on the
+ * launching stream and accumulates, per kernel, the device time and the
+ * launch count. srt3d_profile_enable(ctx, 1) clears the totals and starts
+ * recording, 0 stops. srt3d_profile_read() waits for the recorded events and
+ * returns the totals of kernel `kernel` (an index < srt3d_kernel_count()). */
+srt3d_status srt3d_profile_enable(srt3d_ctx* ctx, int enable);
+srt3d_status srt3d_profile_read(srt3d_ctx* ctx, uint32_t kernel, double* total_ms, uint64_t* launches);
+uint32_t srt3d_kernel_count(void);
+const char* srt3d_kernel_name(uint32_t kernel);
+
 #ifdef __cplusplus
 }
 #endif

@@ -217,3 +217,40 @@ def srt3d_poll(ctx, frame_id, timeout_us, depth, alpha, active, alpha0, n=None, 
                           _host(alpha, np.float32, "alpha"), _host(active, np.uint8, "active"),
                           _host(alpha0, np.float32, "alpha0"), _host(n, np.uint32, "n"))
     return _check(ctx, st, "srt3d_poll") if check else st
+
+
+_SIGS.update({
+    "srt3d_profile_enable": (_i32, [_vp, _i32]),
+    "srt3d_profile_read": (_i32, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
+    "srt3d_kernel_count": (_u32, []),
+    "srt3d_kernel_name": (ctypes.c_char_p, [_u32]),
+})
+
+
+def srt3d_profile_enable(ctx, enable=True):
+    return _check(ctx, lib().srt3d_profile_enable(ctx, int(bool(enable))), "srt3d_profile_enable")
+
+
+def srt3d_profile_read(ctx, kernel):
+    ms = ctypes.c_double()
+    cnt = ctypes.c_uint64()
+    _check(ctx, lib().srt3d_profile_read(ctx, int(kernel), ctypes.byref(ms), ctypes.byref(cnt)), "srt3d_profile_read")
+    return ms.value, cnt.value
+
+
+def srt3d_kernel_count():
+    return int(lib().srt3d_kernel_count())
+
+
+def srt3d_kernel_name(kernel):
+    return lib().srt3d_kernel_name(int(kernel)).decode()
+
+
+def profile_totals(ctx):
+    """{kernel name: (total ms, launches)} for every kernel with launches."""
+    out = {}
+    for k in range(srt3d_kernel_count()):
+        ms, cnt = srt3d_profile_read(ctx, k)
+        if cnt:
+            out[srt3d_kernel_name(k)] = (ms, cnt)
+    return out

@@ -41,6 +41,36 @@ struct DevBuf {
 
 struct Serving;  // serving runtime (serve.cu)
 
+// Kernel ids for the profiling counters.
+enum KernelId : uint32_t {
+  KID_SKETCH_STREAM = 0,
+  KID_FINALIZE,
+  KID_HIST_FROM_STREAM,
+  KID_SKETCH_HIST_FP32,
+  KID_SKETCH_HIST_TC,
+  KID_PREP,
+  KID_INIT,
+  KID_GRAD,
+  KID_NORMALS,
+  KID_SPHERE,
+  KID_ALPHA0,
+  KID_COUNT
+};
+
+// Per-kernel CUDA-event timing (enabled by srt3d_profile_enable).
+struct Profiler {
+  bool enabled = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending {
+    uint32_t kid;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  double total_ms[KID_COUNT] = {};
+  uint64_t launches[KID_COUNT] = {};
+  std::mutex mu;
+};
+
 }  // namespace srt3d
 
 struct srt3d_ctx {
@@ -59,6 +89,7 @@ struct srt3d_ctx {
   srt3d::Serving* serving = nullptr;
   // autotuned launch shapes: key -> value
   std::map<uint64_t, int> tuned;
+  srt3d::Profiler prof;
 };
 
 namespace srt3d {
@@ -86,6 +117,14 @@ srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint3
                              const srt3d_params* prm);
 
 void serving_destroy(srt3d_ctx* ctx);
+
+// Profiling: prof_begin returns an event pair (or {nullptr,nullptr} when off)
+// recorded around one launch on `stream`.
+struct ProfMark {
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+ProfMark prof_begin(srt3d_ctx* ctx, uint32_t kid, cudaStream_t stream);
+void prof_end(srt3d_ctx* ctx, uint32_t kid, const ProfMark& mk, cudaStream_t stream);
 
 }  // namespace srt3d
 

@@ -536,7 +536,11 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
     SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   }
-  k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
+  {
+    const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
+    k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
+    prof_end(ctx, KID_PREP, mk, stream);
+  }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   if (prm.init_mode == SRT3D_INIT_MATCHED) {
     int bps = 0;
@@ -545,11 +549,19 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     const uint32_t wpb = kBlock / 32;
     const uint64_t need = (uint64_t(P) + wpb - 1) / wpb;
     const uint32_t grid = uint32_t(std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps));
-    k_init<K><<<grid, kBlock, tab_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, sc.hh, sc.misc,
+    {
+      const ProfMark mk = prof_begin(ctx, KID_INIT, stream);
+      k_init<K><<<grid, kBlock, tab_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, sc.hh, sc.misc,
                                                   prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
+      prof_end(ctx, KID_INIT, mk, stream);
+    }
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   } else {
-    k_alpha0<K><<<(P + kBlock - 1) / kBlock, kBlock, 0, stream>>>(P, alpha, active, alpha0);
+    {
+      const ProfMark mk = prof_begin(ctx, KID_ALPHA0, stream);
+      k_alpha0<K><<<(P + kBlock - 1) / kBlock, kBlock, 0, stream>>>(P, alpha, active, alpha0);
+      prof_end(ctx, KID_ALPHA0, mk, stream);
+    }
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   }
   const uint32_t grid = (P + kBlock - 1) / kBlock;
@@ -563,16 +575,32 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   st.ds = prm.depth_scale;
   for (uint32_t it = 0; it < prm.iters; ++it) {
     if (!prm.regularize) {
-      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, depth, alpha,
+      {
+        const ProfMark mk = prof_begin(ctx, KID_GRAD, stream);
+        k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, depth, alpha,
                                              nullptr, alpha0);
+        prof_end(ctx, KID_GRAD, mk, stream);
+      }
       SRT3D_CUDA_TRY(ctx, cudaGetLastError());
       continue;
     }
-    k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, sc.t1, sc.a1,
+    {
+      const ProfMark mk = prof_begin(ctx, KID_GRAD, stream);
+      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, sc.t1, sc.a1,
                                            sc.act1, nullptr);
-    k_normals<K><<<grid, kBlock, 0, stream>>>(st, sc.t1, sc.act1, sc.nrm);
-    k_sphere<K><<<grid, kBlock, 0, stream>>>(st, prm.smooth_lambda, prm.prune_alpha, sc.t1, sc.a1, sc.act1, sc.nrm,
+      prof_end(ctx, KID_GRAD, mk, stream);
+    }
+    {
+      const ProfMark mk = prof_begin(ctx, KID_NORMALS, stream);
+      k_normals<K><<<grid, kBlock, 0, stream>>>(st, sc.t1, sc.act1, sc.nrm);
+      prof_end(ctx, KID_NORMALS, mk, stream);
+    }
+    {
+      const ProfMark mk = prof_begin(ctx, KID_SPHERE, stream);
+      k_sphere<K><<<grid, kBlock, 0, stream>>>(st, prm.smooth_lambda, prm.prune_alpha, sc.t1, sc.a1, sc.act1, sc.nrm,
                                              depth, alpha, active, alpha0);
+      prof_end(ctx, KID_SPHERE, mk, stream);
+    }
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   }
   return SRT3D_OK;

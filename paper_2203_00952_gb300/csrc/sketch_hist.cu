@@ -119,8 +119,10 @@ srt3d_status launch_sketch_hist_fp32(srt3d_ctx* ctx, const uint16_t* hist, uint3
     SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_hist_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem)));
   const uint32_t grid = (P + kTileP - 1) / kTileP;
+  const ProfMark mk = prof_begin(ctx, KID_SKETCH_HIST_FP32, stream);
   k_sketch_hist_fp32<<<grid, 256, smem, stream>>>(hist, P, T, m, tab.dev, tab.entries, tab.two_level ? 1 : 0, S,
                                                   n);
+  prof_end(ctx, KID_SKETCH_HIST_FP32, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }

@@ -232,9 +232,11 @@ srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const 
   const uint64_t groups_per_block = kBlock >> glog2;
   const uint64_t need = (uint64_t(P) + groups_per_block - 1) / groups_per_block;
   const uint64_t grid = std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps);
+  const ProfMark mk = prof_begin(ctx, KID_SKETCH_STREAM, stream);
   fn<<<dim3(uint32_t(grid)), dim3(kBlock), smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, m, glog2,
                                                           accumulate, tab.dev, tab.entries, tab.two_level ? 1 : 0,
                                                           S, n, ctx->d_flags);
+  prof_end(ctx, KID_SKETCH_STREAM, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }
@@ -243,7 +245,9 @@ srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n,
                              float2* z, cudaStream_t stream) {
   const size_t total = size_t(P) * m;
   const uint32_t grid = uint32_t((total + kBlock - 1) / kBlock);
+  const ProfMark mk = prof_begin(ctx, KID_FINALIZE, stream);
   k_finalize<<<grid, kBlock, 0, stream>>>(S, n, P, m, z);
+  prof_end(ctx, KID_FINALIZE, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }
@@ -258,8 +262,10 @@ srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, con
   SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hist_from_stream, kBlock, smem));
   if (bps < 1) bps = 1;
   const uint32_t grid = uint32_t(std::min<uint64_t>(P, uint64_t(ctx->num_sms) * bps));
+  const ProfMark mk = prof_begin(ctx, KID_HIST_FROM_STREAM, stream);
   k_hist_from_stream<<<grid, kBlock, smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, hist,
                                                      ctx->d_flags);
+  prof_end(ctx, KID_HIST_FROM_STREAM, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }
