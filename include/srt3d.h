@@ -179,6 +179,29 @@ srt3d_status srt3d_reconstruct(srt3d_ctx* ctx, const float* z, const uint32_t* n
                                const srt3d_params* params, float* depth, float* alpha,
                                uint8_t* active, float* alpha0, void* stream);
 
+/* Allocation-free variant of srt3d_reconstruct (the paper has no
+ * counterpart; same arguments and results). For callers that cannot allocate
+ * device memory while they reconstruct: a real-time lidar loop in which
+ * cudaMalloc/cudaFree (which may synchronise the device and take unbounded
+ * time) is not allowed, or a process whose device memory is wholly reserved
+ * by another allocator. It calls no cudaMalloc, cudaFree or other allocating
+ * routine: its scratch and phase table live in one 16 MiB file-scope device
+ * array that every GPU loading libsrt3d.so holds until the process exits.
+ *   Limit: rows * cols * k_max <= 655360 points (e.g. 512x512 with k_max = 2);
+ *   larger frames are rejected with SRT3D_EINVAL and a message.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device made current); make that first call before any
+ *   stream capture.
+ *   All calls share the array and it keeps the last call's contents (every
+ *   word is rewritten before use, nothing needs clearing): calls that overlap
+ *   on the GPU (different streams or contexts of the same device) race and
+ *   must be serialised by the caller.
+ *   Profiling (srt3d_profile_enable) must be off: it creates CUDA events. */
+srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z, const uint32_t* n, uint32_t rows,
+                                       uint32_t cols, uint32_t T, uint32_t m, const float* h,
+                                       const srt3d_params* params, float* depth, float* alpha,
+                                       uint8_t* active, float* alpha0, void* stream);
+
 /* Serving (continuous batching). A frame is opened by its first chunk,
  * receives photon chunks as host CSR arrays that are sketched online into a
  * device-resident per-pixel state, and is reconstructed after its last chunk.

@@ -224,7 +224,22 @@ _SIGS.update({
     "srt3d_profile_read": (_i32, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "srt3d_kernel_count": (_u32, []),
     "srt3d_kernel_name": (ctypes.c_char_p, [_u32]),
+    "srt3d_reconstruct_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, ctypes.POINTER(srt3d_params),
+                                         _vp, _vp, _vp, _vp, _vp]),
 })
+
+
+def srt3d_reconstruct_noalloc(ctx, z, n, rows, cols, T, m, h, params, depth, alpha, active, alpha0, stream=None,
+                              check=True):
+    """Allocation-free reconstruction (see include/srt3d.h)."""
+    import torch
+
+    st = lib().srt3d_reconstruct_noalloc(ctx, _dev(z, torch.float32, "z"), _dev(n, torch.int32, "n"), int(rows),
+                                         int(cols), int(T), int(m), _dev(h, torch.float32, "h"),
+                                         ctypes.byref(params), _dev(depth, torch.float32, "depth"),
+                                         _dev(alpha, torch.float32, "alpha"), _dev(active, torch.uint8, "active"),
+                                         _dev(alpha0, torch.float32, "alpha0"), _stream(stream))
+    return _check(ctx, st, "srt3d_reconstruct_noalloc") if check else st
 
 
 def srt3d_profile_enable(ctx, enable=True):

@@ -654,3 +654,94 @@ extern "C" srt3d_status srt3d_reconstruct(srt3d_ctx* ctx, const float* z, const 
                           active, alpha0, ctx->rc_scratch.ptr, ctx->rc_scratch.bytes,
                           static_cast<cudaStream_t>(stream));
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of srt3d_reconstruct.
+//
+// Some callers cannot allocate device memory at the moment they reconstruct a
+// frame: a lidar front-end that runs the reconstruction inside a hard
+// real-time loop (cudaMalloc / cudaFree may synchronise the whole device and
+// take unbounded time), or a process whose device memory is entirely reserved
+// by another allocator. srt3d_reconstruct_noalloc serves them: its scratch
+// (post-gradient state, normals, hhat, step sizes) and its phase table live in
+// one file-scope __device__ array of fixed size that every GPU loading this
+// library holds until exit. The launches are the ones srt3d_reconstruct uses.
+namespace srt3d {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;                   // whole array: 16 MiB
+constexpr size_t kNoAllocTableBytes = size_t(kDirectTableMax) * sizeof(float2);  // 64 KiB
+constexpr size_t kNoAllocScratchMax = kNoAllocBytes - kNoAllocTableBytes;
+constexpr int kNoAllocMaxDevices = 64;
+constexpr uint64_t kNoAllocMaxPoints = 655360;  // rows * cols * k_max
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+
+// cos/sin(2 pi k / T) in double, rounded once to float: the same values the
+// host builds for the allocating path.
+__global__ void k_noalloc_phase_table(uint32_t T, uint32_t entries, int two_level, float2* __restrict__ tab) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= entries) return;
+  const double k = two_level ? (i < 256u ? double(i) : 256.0 * double(i - 256u)) : double(i);
+  double s, c;
+  sincospi(2.0 * k / double(T), &s, &c);
+  tab[i] = make_float2(float(c), float(s));
+}
+
+}  // namespace
+}  // namespace srt3d
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[srt3d::kNoAllocBytes];
+
+extern "C" srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z, const uint32_t* n, uint32_t rows,
+                                                  uint32_t cols, uint32_t T, uint32_t m, const float* h,
+                                                  const srt3d_params* params, float* depth, float* alpha,
+                                                  uint8_t* active, float* alpha0, void* stream) {
+  using namespace srt3d;
+  if (!ctx) return SRT3D_EINVAL;
+  srt3d_status st = validate_params(ctx, rows, cols, T, m, params);
+  if (st != SRT3D_OK) return st;
+  if (!z || !n || !h || !depth || !alpha || !active || !alpha0) return set_error(ctx, SRT3D_EINVAL, "NULL pointer");
+  if (reinterpret_cast<uintptr_t>(z) % 8) return set_error(ctx, SRT3D_EINVAL, "z must be 8-byte aligned");
+  if (ctx->prof.enabled)
+    return set_error(ctx, SRT3D_EINVAL, "srt3d_reconstruct_noalloc: disable profiling (it creates CUDA events)");
+  const uint32_t P = rows * cols;
+  const size_t need = reconstruct_scratch_bytes(P, params->k_max, m);
+  if (uint64_t(P) * params->k_max > kNoAllocMaxPoints || need > kNoAllocScratchMax)
+    return set_error(ctx, SRT3D_EINVAL,
+                     "srt3d_reconstruct_noalloc: frame too large for the static scratch (rows*cols*k_max must be "
+                     "<= 655360 points)");
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return set_error(ctx, SRT3D_EINVAL, "srt3d_reconstruct_noalloc: device index out of range");
+  // Set-up once per device, with that device current: the array's device address.
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+      int cur = -1;
+      SRT3D_CUDA_TRY(ctx, cudaGetDevice(&cur));
+      if (cur != ctx->device) SRT3D_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (cur != ctx->device) cudaSetDevice(cur);
+      if (e != cudaSuccess) return cuda_error(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+      g_noalloc_addr[ctx->device] = p;
+    }
+    base = g_noalloc_addr[ctx->device];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Phase table at the end of the array, rebuilt on every call (every word of
+  // the array is written before it is read within a call; nothing needs clearing).
+  PhaseTable tab;
+  tab.two_level = T > kDirectTableMax;
+  tab.entries = tab.two_level ? 256u + (T + 255u) / 256u : T;
+  tab.dev = reinterpret_cast<float2*>(static_cast<char*>(base) + kNoAllocScratchMax);
+  k_noalloc_phase_table<<<(tab.entries + 255u) / 256u, 256, 0, s>>>(T, tab.entries, tab.two_level ? 1 : 0, tab.dev);
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  const Scratch sc = carve(base, P, params->k_max);
+  const float2* zz = reinterpret_cast<const float2*>(z);
+  if (params->k_max == 1)
+    return run<1>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+  return run<2>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+}
