@@ -213,6 +213,12 @@ def kernel_work(name, N, P, m, T, K, iters):
     if name == "init":
         # per pixel, pass and candidate depth: m complex Horner steps (4 FFMA)
         return "alu", P * K * T * 4 * m / 1e12, "Tinst"
+    if name == "iter":
+        # per point and iteration: the gradient step (14 FP32 instr per
+        # harmonic per point) and, per neighbour slot of the (2r+1)^2 x K
+        # window, the APSS weight and moments for the normal (~25 instr) and
+        # for the sphere and smoothing (~30 instr)
+        return "alu", P * K * (14 * m + 9 * K * 55) / 1e12, "Tinst"
     if name == "finalize":
         return "hbm", (P * m * 16 + P * 4) / 1e9, "GB"
     return None, None, None

@@ -51,8 +51,7 @@ enum KernelId : uint32_t {
   KID_PREP,
   KID_INIT,
   KID_GRAD,
-  KID_NORMALS,
-  KID_SPHERE,
+  KID_ITER,
   KID_ALPHA0,
   KID_COUNT
 };

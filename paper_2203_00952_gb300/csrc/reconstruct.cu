@@ -7,18 +7,20 @@
 //   k_prep    hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau} (Eq. 4), the global
 //             step sizes, and n_max
 //   k_init    sketched matched filter: argmax over integer t of
-//             Re sum_l conj(hhat_l e^{i w_l t}) z_l (Horner in w = e^{-i 2pi t/T}),
-//             alpha = s / sum|hhat|^2, second surface from the residual
-//   per iteration:
-//   k_grad    Jacobi gradient step on n ||z - Psi||^2 (t, alpha), alpha >= 0,
-//             sum alpha <= 1
-//   k_normals weighted least-squares plane over the (2r+1)^2 x K neighbours
-//             gated by |dt| <= d_max and the APSS weight (1 - d^2/h^2)^4
-//   k_sphere  algebraic sphere fit with normals (Guennebaud & Gross 2007)
-//             and projection along the line of sight; intensity smoothing,
-//             pruning, alpha_0 = 1 - sum alpha
+//             Re sum_l conj(hhat_l e^{i w_l t}) z_l (Horner in w = e^{-i 2pi t/T},
+//             exact branch and bound on a coarse grid), alpha = s / sum|hhat|^2,
+//             second surface from the residual
+//   per iteration, one fused tile kernel (k_iter):
+//             Jacobi gradient step on n ||z - Psi||^2 (t, alpha), alpha >= 0,
+//             sum alpha <= 1; weighted least-squares plane normals over the
+//             (2r+1)^2 x K neighbours gated by |dt| <= d_max and the APSS weight
+//             (1 - d^2/h^2)^4; algebraic sphere fit with normals (Guennebaud &
+//             Gross 2007) and projection along the line of sight; intensity
+//             smoothing, pruning, alpha_0 = 1 - sum alpha
+//   k_grad    the gradient step alone (pixelwise mode, no spatial prior)
 // The iteration state lives in the caller's depth/alpha/active buffers; the
-// post-gradient state, normals, hhat and step sizes live in a scratch block.
+// post-gradient state and the normals live in shared memory; hhat and the
+// step sizes live in a scratch block.
 #include <cfloat>
 #include <cmath>
 
@@ -144,42 +146,119 @@ __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, cons
   }
 }
 
-// Horner evaluation of Re sum_{l=1}^{m} c_l w^l, w = e^{-i 2 pi t / T}; one
-// lane per t, best (score, smallest t) per warp.
+// Matched-filter score s(t) = Re sum_{l=1}^{m} c_l w^l, w = e^{-i 2 pi t / T},
+// by complex Horner (4 FFMA per harmonic).
+__device__ __forceinline__ float mf_score(const float2* c, uint32_t m, const float2* s_tab, bool tl, uint32_t t) {
+  float2 w = phase(s_tab, t, tl);
+  w.y = -w.y;
+  float ax = c[m - 1].x, ay = c[m - 1].y;
+  for (int l = int(m) - 2; l >= 0; --l) {
+    const float nx = fmaf(ax, w.x, fmaf(-ay, w.y, c[l].x));
+    const float ny = fmaf(ax, w.y, fmaf(ay, w.x, c[l].y));
+    ax = nx;
+    ay = ny;
+  }
+  return fmaf(ax, w.x, -ay * w.y);
+}
+
+__device__ __forceinline__ bool mf_allowed(uint32_t t, int excl_t, float min_sep, uint32_t T) {
+  if (excl_t < 0) return true;
+  const uint32_t d0 = t > uint32_t(excl_t) ? t - uint32_t(excl_t) : uint32_t(excl_t) - t;
+  return float(min(d0, T - d0)) >= min_sep;
+}
+
+__device__ __forceinline__ void mf_take(float s, uint32_t t, float& bs, uint32_t& bt) {
+  if (s > bs || (s == bs && t < bt)) {
+    bs = s;
+    bt = t;
+  }
+}
+
+// Exact argmax over integer t in [0, T) (smallest t on ties) of the FP32
+// scores, one warp per pixel, by branch and bound: s is a trigonometric
+// polynomial with |s''| <= M2 = sum_l |c_l| w_l^2, so on an interval of length
+// L between grid points s <= max(endpoints) + M2 L^2 / 8. Scores are evaluated
+// on a grid of spacing D (a power of two, M2 D^2 / 8 <= 0.02 M0,
+// M0 = sum_l |c_l|), and only intervals whose bound (plus a margin covering
+// the FP32 evaluation error of both ends) reaches the best grid score are
+// evaluated point by point. Every t whose FP32 score can be the maximum is
+// evaluated with the same code as an exhaustive scan, so the result equals
+// the exhaustive FP32 argmax.
 __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, uint32_t T, const float2* s_tab,
                                                    bool tl, int excl_t, float min_sep, float* best_s,
                                                    uint32_t* best_t) {
   const uint32_t lane = threadIdx.x & 31u;
+  float m0 = 0.f, m2 = 0.f;
+  for (uint32_t l = lane; l < m; l += 32u) {
+    const float a = sqrtf(c[l].x * c[l].x + c[l].y * c[l].y);
+    const float w = 6.283185307179586f * float(l + 1u) / float(T);
+    m0 += a;
+    m2 += a * w * w;
+  }
+  for (int off = 16; off; off >>= 1) {
+    m0 += __shfl_xor_sync(0xffffffffu, m0, off);
+    m2 += __shfl_xor_sync(0xffffffffu, m2, off);
+  }
+  if (m0 == 0.f) {  // all scores are exactly 0: the smallest allowed t wins
+    for (uint32_t t0 = 0; t0 < T; t0 += 32u) {
+      const uint32_t t = t0 + lane;
+      const unsigned ok = __ballot_sync(0xffffffffu, t < T && mf_allowed(t, excl_t, min_sep, T));
+      if (ok) {
+        *best_s = 0.f;
+        *best_t = t0 + uint32_t(__ffs(ok)) - 1u;
+        return;
+      }
+    }
+    *best_s = -FLT_MAX;
+    *best_t = 0xffffffffu;
+    return;
+  }
+  m2 *= 1.01f;
+  uint32_t D = 64u;
+  while (D > 1u && m2 * float(D * D) * 0.125f > 0.02f * m0) D >>= 1;
+  const uint32_t G = (T + D - 1u) / D;
+  const float margin = 4e-5f * m0 + 1e-30f;
   float bs = -FLT_MAX;
   uint32_t bt = 0xffffffffu;
-  for (uint32_t t = lane; t < T; t += 32u) {
-    if (excl_t >= 0) {
-      const uint32_t d0 = t > uint32_t(excl_t) ? t - uint32_t(excl_t) : uint32_t(excl_t) - t;
-      const uint32_t d = min(d0, T - d0);
-      if (float(d) < min_sep) continue;
-    }
-    float2 w = phase(s_tab, t, tl);
-    w.y = -w.y;
-    float ax = c[m - 1].x, ay = c[m - 1].y;
-    for (int l = int(m) - 2; l >= 0; --l) {
-      const float nx = fmaf(ax, w.x, fmaf(-ay, w.y, c[l].x));
-      const float ny = fmaf(ax, w.y, fmaf(ay, w.x, c[l].y));
-      ax = nx;
-      ay = ny;
-    }
-    const float s = fmaf(ax, w.x, -ay * w.y);
-    if (s > bs) {
-      bs = s;
-      bt = t;
+  // grid points
+  for (uint32_t g = lane; g < G; g += 32u) {
+    const uint32_t t = g * D;
+    if (!mf_allowed(t, excl_t, min_sep, T)) continue;
+    mf_take(mf_score(c, m, s_tab, tl, t), t, bs, bt);
+  }
+  float best_grid = bs;
+  for (int off = 16; off; off >>= 1) best_grid = fmaxf(best_grid, __shfl_xor_sync(0xffffffffu, best_grid, off));
+  // intervals whose bound reaches the best grid score
+  if (D > 1u) {
+    for (uint32_t base = 0; base < G; base += 32u) {
+      const uint32_t i = base + lane;
+      bool surv = false;
+      if (i < G) {
+        const uint32_t a = i * D;
+        const uint32_t len = min(D, T - a);
+        if (len > 1u) {
+          const float sa = mf_score(c, m, s_tab, tl, a);
+          const float sb = mf_score(c, m, s_tab, tl, (a + len) % T);
+          surv = fmaxf(sa, sb) + m2 * float(len * len) * 0.125f + margin >= best_grid;
+        }
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, surv);
+      while (mask) {
+        const uint32_t j = uint32_t(__ffs(mask)) - 1u;
+        mask &= mask - 1u;
+        const uint32_t a = (base + j) * D;
+        const uint32_t len = min(D, T - a);
+        for (uint32_t t = a + 1u + lane; t < a + len; t += 32u) {
+          if (!mf_allowed(t, excl_t, min_sep, T)) continue;
+          mf_take(mf_score(c, m, s_tab, tl, t), t, bs, bt);
+        }
+      }
     }
   }
   for (int off = 16; off; off >>= 1) {
     const float os = __shfl_xor_sync(0xffffffffu, bs, off);
     const uint32_t ot = __shfl_xor_sync(0xffffffffu, bt, off);
-    if (os > bs || (os == bs && ot < bt)) {
-      bs = os;
-      bt = ot;
-    }
+    mf_take(os, ot, bs, bt);
   }
   *best_s = bs;
   *best_t = bt;
@@ -274,32 +353,16 @@ __global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, c
   }
 }
 
-// Sketched gradient step (Jacobi), one thread per pixel. With `direct` the
-// result is the new state (pixelwise mode); otherwise it goes to scratch for
-// the denoisers.
+// Sketched gradient step (Jacobi) of one pixel's K points: reads the state
+// (t, a, act), returns the post-step (t, a); inactive points keep t, get a = 0.
 template <int K>
-__global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, const uint32_t* __restrict__ n,
-                                                 uint32_t P, uint32_t T, uint32_t m,
-                                                 const float2* __restrict__ hh_g, const float* __restrict__ misc,
-                                                 const float* depth, const float* alpha, const uint8_t* active,
-                                                 float* t_out, float* a_out, uint8_t* act_out, float* alpha0_out) {
-  __shared__ float2 s_hh[kMaxM];
-  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
-  __syncthreads();
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P) return;
+__device__ __forceinline__ void grad_pixel(const float2* __restrict__ zp, uint32_t cnt, uint32_t T, uint32_t m,
+                                           const float2* s_hh, float eta_t, float eta_a, float (&t)[K],
+                                           float (&a)[K], const bool (&act)[K]) {
   const float Tf = float(T);
-  const float nmax = misc[MISC_NMAX];
-  const float eta_t = misc[MISC_ETA_T] / nmax;
-  const float eta_a = misc[MISC_ETA_A] / nmax;
-  float t[K], a[K];
-  bool act[K];
   float2 e1[K], E[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    t[k] = depth[size_t(p) * K + k];
-    a[k] = alpha[size_t(p) * K + k];
-    act[k] = active[size_t(p) * K + k] != 0;
     float sn, cs;
     sincospif(2.f * t[k] / Tf, &sn, &cs);
     e1[k] = make_float2(cs, sn);
@@ -309,7 +372,6 @@ __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, c
 #pragma unroll
   for (int k = 0; k < K; ++k) gt[k] = ga[k] = 0.f;
   const float wstep = 6.283185307179586f / Tf;
-  const float2* zp = z + size_t(p) * m;
   for (uint32_t l = 0; l < m; ++l) {
     const float2 hv = s_hh[l];
     const float2 zl = zp[l];
@@ -332,7 +394,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, c
       E[k] = cmul(E[k], e1[k]);
     }
   }
-  const float nn = -2.f * float(n[p]);
+  const float nn = -2.f * float(cnt);
   float sum = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -352,147 +414,240 @@ __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, c
 #pragma unroll
     for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
   }
+}
+
+// Pixelwise iteration (regularize = 0): the gradient step is the new state.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, const uint32_t* __restrict__ n,
+                                                 uint32_t P, uint32_t T, uint32_t m,
+                                                 const float2* __restrict__ hh_g, const float* __restrict__ misc,
+                                                 float* depth, float* alpha, const uint8_t* active, float* alpha0) {
+  __shared__ float2 s_hh[kMaxM];
+  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
+  __syncthreads();
+  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float nmax = misc[MISC_NMAX];
+  float t[K], a[K];
+  bool act[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    t[k] = depth[size_t(p) * K + k];
+    a[k] = alpha[size_t(p) * K + k];
+    act[k] = active[size_t(p) * K + k] != 0;
+  }
+  grad_pixel<K>(z + size_t(p) * m, n[p], T, m, s_hh, misc[MISC_ETA_T] / nmax, misc[MISC_ETA_A] / nmax, t, a, act);
   float s2 = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    t_out[size_t(p) * K + k] = t[k];
-    a_out[size_t(p) * K + k] = a[k];
+    depth[size_t(p) * K + k] = t[k];
+    alpha[size_t(p) * K + k] = a[k];
     s2 += a[k];
-    if (act_out) act_out[size_t(p) * K + k] = act[k] ? 1 : 0;
   }
-  if (alpha0_out) alpha0_out[p] = 1.f - s2;
+  alpha0[p] = 1.f - s2;
 }
 
 struct Stencil {
   uint32_t rows, cols, radius;
-  float h2, inv_h2, d_max, ds;
+  float h2, inv_h2, d_max, ds, lambda, prune_alpha;
 };
 
-// Neighbour visitor shared by the two denoiser kernels: calls f(dx, dy, dz, w, q, k2)
-// for every active neighbour point with positive APSS weight (query included).
-template <int K, typename F>
-__device__ __forceinline__ void for_neighbours(const Stencil st, uint32_t r0, uint32_t c0, float tq,
-                                               const float* __restrict__ t1, const uint8_t* __restrict__ act1,
-                                               F&& f) {
-  const int R = int(st.radius);
-  for (int dr = -R; dr <= R; ++dr) {
-    const int rr = int(r0) + dr;
-    if (rr < 0 || rr >= int(st.rows)) continue;
-    for (int dc = -R; dc <= R; ++dc) {
-      const int cc = int(c0) + dc;
-      if (cc < 0 || cc >= int(st.cols)) continue;
-      const uint32_t q = uint32_t(rr) * st.cols + uint32_t(cc);
-#pragma unroll
-      for (int k2 = 0; k2 < K; ++k2) {
-        if (!act1[size_t(q) * K + k2]) continue;
-        const float dt = t1[size_t(q) * K + k2] - tq;
-        if (fabsf(dt) > st.d_max) continue;
-        const float dz = dt * st.ds;
-        const float fx = float(dc), fy = float(dr);
-        const float d2 = fx * fx + fy * fy + dz * dz;
-        if (d2 >= st.h2) continue;
-        const float u = 1.f - d2 * st.inv_h2;
-        const float u2 = u * u;
-        f(fx, fy, dz, u2 * u2, q, k2);
+// APSS weight of a neighbour at pixel offset (dx, dy) and depth offset dt
+// (bins), or a negative value when it is not a neighbour.
+__device__ __forceinline__ float apss_weight(const Stencil& st, float dx, float dy, float dt, float& dz) {
+  if (fabsf(dt) > st.d_max) return -1.f;
+  dz = dt * st.ds;
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  if (d2 >= st.h2) return -1.f;
+  const float u = 1.f - d2 * st.inv_h2;
+  const float u2 = u * u;
+  return u2 * u2;
+}
+
+// Unit normal from the weighted plane-fit moments (z = a + b x + c y).
+__device__ __forceinline__ float4 plane_normal(int cnt, float Sw, float Sx, float Sy, float Sz, float Sxx, float Sxy,
+                                               float Syy, float Sxz, float Syz) {
+  const float det = Sw * (Sxx * Syy - Sxy * Sxy) - Sx * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Sxy - Sxx * Sy);
+  if (cnt >= 3 && det > 1e-6f * Sw * Sw * Sw) {
+    const float db = Sw * (Sxz * Syy - Sxy * Syz) - Sz * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Syz - Sxz * Sy);
+    const float dcf = Sw * (Sxx * Syz - Sxz * Sxy) - Sx * (Sx * Syz - Sxz * Sy) + Sz * (Sx * Sxy - Sxx * Sy);
+    const float b = db / det, c = dcf / det;
+    const float inv = 1.f / sqrtf(b * b + c * c + 1.f);
+    return make_float4(-b * inv, -c * inv, inv, 0.f);
+  }
+  return make_float4(0.f, 0.f, 1.f, 0.f);
+}
+
+// Depth after projecting onto the algebraic sphere fitted from the sums
+// (Guennebaud & Gross 2007, with normals); tq when the fit is rejected.
+__device__ __forceinline__ float sphere_depth(const Stencil& st, float tq, int cnt, float Sw, float Spx, float Spy,
+                                              float Spz, float Snx, float Sny, float Snz, float Spn, float Spp) {
+  const float den = Spp - (Spx * Spx + Spy * Spy + Spz * Spz) / Sw;
+  if (cnt >= 3 && den > 0.f) {
+    const float u4 = 0.5f * (Spn - (Spx * Snx + Spy * Sny + Spz * Snz) / Sw) / den;
+    const float ux = (Snx - 2.f * u4 * Spx) / Sw;
+    const float uy = (Sny - 2.f * u4 * Spy) / Sw;
+    const float uz = (Snz - 2.f * u4 * Spz) / Sw;
+    const float u0 = -(ux * Spx + uy * Spy + uz * Spz + u4 * Spp) / Sw;
+    const float disc = uz * uz - 4.f * u4 * u0;
+    if (disc >= 0.f) {
+      const float sq = sqrtf(disc);
+      const float qq = -0.5f * (uz + (uz >= 0.f ? sq : -sq));
+      if (qq != 0.f) {
+        const float zn = u0 / qq;
+        const float zf = (u4 != 0.f) ? qq / u4 : INFINITY;
+        const float zs = (fabsf(zf) < fabsf(zn)) ? zf : zn;
+        if (fabsf(zs) <= st.d_max * st.ds) return tq + zs / st.ds;
       }
     }
   }
+  return tq;
 }
 
-template <int K>
-__global__ void __launch_bounds__(kBlock, 4) k_normals(Stencil st, const float* __restrict__ t1,
-                                                    const uint8_t* __restrict__ act1, float4* __restrict__ nrm) {
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= st.rows * st.cols) return;
-  const uint32_t r0 = p / st.cols, c0 = p - r0 * st.cols;
+// One SRT3D iteration on a TW x TH tile, fused: the gradient step on the tile
+// plus a 2R halo, plane-fit normals on the tile plus an R halo, then the
+// sphere projection, intensity smoothing and pruning on the tile. The
+// post-gradient state and the normals stay in shared memory; the state is
+// read from and written to global memory once.
+constexpr int kTW = 16, kTH = 16;
+
+template <int K, int R>
+__global__ void __launch_bounds__(kTW* kTH) k_iter(Stencil st, const float2* __restrict__ z,
+                                                   const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
+                                                   const float2* __restrict__ hh_g, const float* __restrict__ misc,
+                                                   float* depth, float* alpha, uint8_t* active, float* alpha0) {
+  constexpr int H = 2 * R;
+  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
+  constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
+  __shared__ float s_t[RH * RW][K];
+  __shared__ float s_a[RH * RW][K];
+  __shared__ uint8_t s_act[RH * RW][K];
+  __shared__ float4 s_n[NH * NW][K];
+  __shared__ float2 s_hh[kMaxM];
+  const int tid = threadIdx.x;
+  if (tid < int(m)) s_hh[tid] = hh_g[tid];
+  __syncthreads();
+  const int r0 = int(blockIdx.y) * kTH, c0 = int(blockIdx.x) * kTW;
+  const float nmax = misc[MISC_NMAX];
+  const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
+  // 1) gradient step on the region (pixels outside the array are inactive)
+  for (int i = tid; i < RH * RW; i += kTW * kTH) {
+    const int rr = r0 - H + i / RW, cc = c0 - H + i % RW;
+    float t[K], a[K];
+    bool act[K];
+    if (rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols)) {
+      const size_t p = size_t(rr) * st.cols + size_t(cc);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    float4 out = make_float4(0.f, 0.f, 1.f, 0.f);
-    if (act1[size_t(p) * K + k]) {
-      const float tq = t1[size_t(p) * K + k];
-      float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
-      int cnt = 0;
-      for_neighbours<K>(st, r0, c0, tq, t1, act1, [&](float x, float y, float zz, float w, uint32_t, int) {
-        Sw += w;
-        Sx += w * x;
-        Sy += w * y;
-        Sz += w * zz;
-        Sxx += w * x * x;
-        Sxy += w * x * y;
-        Syy += w * y * y;
-        Sxz += w * x * zz;
-        Syz += w * y * zz;
-        ++cnt;
-      });
-      const float det = Sw * (Sxx * Syy - Sxy * Sxy) - Sx * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Sxy - Sxx * Sy);
-      if (cnt >= 3 && det > 1e-6f * Sw * Sw * Sw) {
-        const float db = Sw * (Sxz * Syy - Sxy * Syz) - Sz * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Syz - Sxz * Sy);
-        const float dcf = Sw * (Sxx * Syz - Sxz * Sxy) - Sx * (Sx * Syz - Sxz * Sy) + Sz * (Sx * Sxy - Sxx * Sy);
-        const float b = db / det, c = dcf / det;
-        const float inv = 1.f / sqrtf(b * b + c * c + 1.f);
-        out = make_float4(-b * inv, -c * inv, inv, 0.f);
+      for (int k = 0; k < K; ++k) {
+        t[k] = depth[p * K + k];
+        a[k] = alpha[p * K + k];
+        act[k] = active[p * K + k] != 0;
+      }
+      grad_pixel<K>(z + p * m, n[p], T, m, s_hh, eta_t, eta_a, t, a, act);
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        t[k] = 0.f;
+        a[k] = 0.f;
+        act[k] = false;
       }
     }
-    nrm[size_t(p) * K + k] = out;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      s_t[i][k] = t[k];
+      s_a[i][k] = a[k];
+      s_act[i][k] = act[k] ? 1 : 0;
+    }
   }
-}
-
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_sphere(Stencil st, float lambda, float prune_alpha,
-                                                   const float* __restrict__ t1, const float* __restrict__ a1,
-                                                   const uint8_t* __restrict__ act1, const float4* __restrict__ nrm,
-                                                   float* __restrict__ depth, float* __restrict__ alpha,
-                                                   uint8_t* __restrict__ active, float* __restrict__ alpha0) {
-  const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= st.rows * st.cols) return;
-  const uint32_t r0 = p / st.cols, c0 = p - r0 * st.cols;
+  __syncthreads();
+  // 2) normals on the tile plus an R halo
+  for (int i = tid; i < NH * NW; i += kTW * kTH) {
+    const int lr = i / NW + R, lc = i % NW + R;  // region coordinates
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float4 nv = make_float4(0.f, 0.f, 1.f, 0.f);
+      const int q0 = lr * RW + lc;
+      if (s_act[q0][k]) {
+        const float tq = s_t[q0][k];
+        float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int dr = -R; dr <= R; ++dr)
+#pragma unroll
+          for (int dc = -R; dc <= R; ++dc) {
+            const int q = (lr + dr) * RW + (lc + dc);
+#pragma unroll
+            for (int k2 = 0; k2 < K; ++k2) {
+              if (!s_act[q][k2]) continue;
+              float dz;
+              const float fx = float(dc), fy = float(dr);
+              const float w = apss_weight(st, fx, fy, s_t[q][k2] - tq, dz);
+              if (w < 0.f) continue;
+              Sw += w;
+              Sx += w * fx;
+              Sy += w * fy;
+              Sz += w * dz;
+              Sxx += w * fx * fx;
+              Sxy += w * fx * fy;
+              Syy += w * fy * fy;
+              Sxz += w * fx * dz;
+              Syz += w * fy * dz;
+              ++cnt;
+            }
+          }
+        nv = plane_normal(cnt, Sw, Sx, Sy, Sz, Sxx, Sxy, Syy, Sxz, Syz);
+      }
+      s_n[i][k] = nv;
+    }
+  }
+  __syncthreads();
+  // 3) sphere projection, smoothing and pruning on the tile
+  const int ty = tid / kTW, tx = tid % kTW;
+  const int rr = r0 + ty, cc = c0 + tx;
+  if (rr >= int(st.rows) || cc >= int(st.cols)) return;
+  const int lr = ty + H, lc = tx + H;
+  const int q0 = lr * RW + lc;
   float tout[K], aout[K];
   bool aact[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float tq = t1[size_t(p) * K + k];
+    const float tq = s_t[q0][k];
     tout[k] = tq;
     aout[k] = 0.f;
     aact[k] = false;
-    if (!act1[size_t(p) * K + k]) continue;
+    if (!s_act[q0][k]) continue;
     float Sw = 0, Spx = 0, Spy = 0, Spz = 0, Snx = 0, Sny = 0, Snz = 0, Spn = 0, Spp = 0, Swa = 0;
     int cnt = 0;
-    for_neighbours<K>(st, r0, c0, tq, t1, act1, [&](float x, float y, float zz, float w, uint32_t q, int k2) {
-      const float4 nv = nrm[size_t(q) * K + k2];
-      Sw += w;
-      Spx += w * x;
-      Spy += w * y;
-      Spz += w * zz;
-      Snx += w * nv.x;
-      Sny += w * nv.y;
-      Snz += w * nv.z;
-      Spn += w * (x * nv.x + y * nv.y + zz * nv.z);
-      Spp += w * (x * x + y * y + zz * zz);
-      Swa += w * a1[size_t(q) * K + k2];
-      ++cnt;
-    });
-    const float den = Spp - (Spx * Spx + Spy * Spy + Spz * Spz) / Sw;
-    if (cnt >= 3 && den > 0.f) {
-      const float u4 = 0.5f * (Spn - (Spx * Snx + Spy * Sny + Spz * Snz) / Sw) / den;
-      const float ux = (Snx - 2.f * u4 * Spx) / Sw;
-      const float uy = (Sny - 2.f * u4 * Spy) / Sw;
-      const float uz = (Snz - 2.f * u4 * Spz) / Sw;
-      const float u0 = -(ux * Spx + uy * Spy + uz * Spz + u4 * Spp) / Sw;
-      const float disc = uz * uz - 4.f * u4 * u0;
-      if (disc >= 0.f) {
-        const float sq = sqrtf(disc);
-        const float qq = -0.5f * (uz + (uz >= 0.f ? sq : -sq));
-        if (qq != 0.f) {
-          const float zn = u0 / qq;
-          const float zf = (u4 != 0.f) ? qq / u4 : INFINITY;
-          const float zs = (fabsf(zf) < fabsf(zn)) ? zf : zn;
-          if (fabsf(zs) <= st.d_max * st.ds) tout[k] = tq + zs / st.ds;
+#pragma unroll
+    for (int dr = -R; dr <= R; ++dr)
+#pragma unroll
+      for (int dc = -R; dc <= R; ++dc) {
+        const int q = (lr + dr) * RW + (lc + dc);
+        const int qn = (lr + dr - R) * NW + (lc + dc - R);
+#pragma unroll
+        for (int k2 = 0; k2 < K; ++k2) {
+          if (!s_act[q][k2]) continue;
+          float dz;
+          const float fx = float(dc), fy = float(dr);
+          const float w = apss_weight(st, fx, fy, s_t[q][k2] - tq, dz);
+          if (w < 0.f) continue;
+          const float4 nv = s_n[qn][k2];
+          Sw += w;
+          Spx += w * fx;
+          Spy += w * fy;
+          Spz += w * dz;
+          Snx += w * nv.x;
+          Sny += w * nv.y;
+          Snz += w * nv.z;
+          Spn += w * (fx * nv.x + fy * nv.y + dz * nv.z);
+          Spp += w * (fx * fx + fy * fy + dz * dz);
+          Swa += w * s_a[q][k2];
+          ++cnt;
         }
       }
-    }
-    const float aq = a1[size_t(p) * K + k];
-    const float an = (1.f - lambda) * aq + lambda * (Swa / Sw);
-    aact[k] = an >= prune_alpha;
+    tout[k] = sphere_depth(st, tq, cnt, Sw, Spx, Spy, Spz, Snx, Sny, Snz, Spn, Spp);
+    const float an = (1.f - st.lambda) * s_a[q0][k] + st.lambda * (Swa / Sw);
+    aact[k] = an >= st.prune_alpha;
     aout[k] = aact[k] ? an : 0.f;
   }
   float sum = 0.f;
@@ -505,11 +660,12 @@ __global__ void __launch_bounds__(kBlock) k_sphere(Stencil st, float lambda, flo
 #pragma unroll
     for (int k = 0; k < K; ++k) sum += aout[k];
   }
+  const size_t p = size_t(rr) * st.cols + size_t(cc);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    depth[size_t(p) * K + k] = tout[k];
-    alpha[size_t(p) * K + k] = aout[k];
-    active[size_t(p) * K + k] = aact[k] ? 1 : 0;
+    depth[p * K + k] = tout[k];
+    alpha[p * K + k] = aout[k];
+    active[p * K + k] = aact[k] ? 1 : 0;
   }
   alpha0[p] = 1.f - sum;
 }
@@ -573,34 +729,21 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   st.inv_h2 = 1.f / st.h2;
   st.d_max = prm.d_max;
   st.ds = prm.depth_scale;
+  st.lambda = prm.smooth_lambda;
+  st.prune_alpha = prm.prune_alpha;
+  const dim3 tiles((cols + kTW - 1) / kTW, (rows + kTH - 1) / kTH);
   for (uint32_t it = 0; it < prm.iters; ++it) {
+    const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);
     if (!prm.regularize) {
-      {
-        const ProfMark mk = prof_begin(ctx, KID_GRAD, stream);
-        k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, depth, alpha,
-                                             nullptr, alpha0);
-        prof_end(ctx, KID_GRAD, mk, stream);
-      }
-      SRT3D_CUDA_TRY(ctx, cudaGetLastError());
-      continue;
+      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+    } else if (prm.radius == 1) {
+      k_iter<K, 1><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+    } else if (prm.radius == 2) {
+      k_iter<K, 2><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+    } else {
+      k_iter<K, 3><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     }
-    {
-      const ProfMark mk = prof_begin(ctx, KID_GRAD, stream);
-      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, sc.t1, sc.a1,
-                                           sc.act1, nullptr);
-      prof_end(ctx, KID_GRAD, mk, stream);
-    }
-    {
-      const ProfMark mk = prof_begin(ctx, KID_NORMALS, stream);
-      k_normals<K><<<grid, kBlock, 0, stream>>>(st, sc.t1, sc.act1, sc.nrm);
-      prof_end(ctx, KID_NORMALS, mk, stream);
-    }
-    {
-      const ProfMark mk = prof_begin(ctx, KID_SPHERE, stream);
-      k_sphere<K><<<grid, kBlock, 0, stream>>>(st, prm.smooth_lambda, prm.prune_alpha, sc.t1, sc.a1, sc.act1, sc.nrm,
-                                             depth, alpha, active, alpha0);
-      prof_end(ctx, KID_SPHERE, mk, stream);
-    }
+    prof_end(ctx, prm.regularize ? KID_ITER : KID_GRAD, mk, stream);
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   }
   return SRT3D_OK;

@@ -271,3 +271,13 @@ def test_invalid_params_rejected(ctx):
         assert ei.value.status == B.SRT3D_EINVAL
     with pytest.raises(B.SRT3DError):
         B.srt3d_reconstruct(ctx, z, n, 2, 2, T, 64, h, B.make_params(), d, a, act, a0)
+
+
+@pytest.mark.parametrize("T,m,sigma", [(8193, 12, 6.0), (65536, 32, 20.0), (64, 3, 1.5)])
+def test_init_large_and_small_T(ctx, T, m, sigma):
+    spec = synth.FrameSpec(rows=6, cols=5, T=T, sigma=sigma, mean_photons=400.0, sbr=1.0, two_surface_frac=0.5,
+                           sep_lo=min(50.0, T / 8), sep_hi=min(300.0, T / 4))
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, 41, m)
+    p = oracle_params(iters=0, k_max=2, d_max=6 * sigma, min_sep=3 * sigma)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, T, m, h32, p)
+    check_init_validity(g[0], g[1], g[2], z_np, n_np, hh, T, p)
