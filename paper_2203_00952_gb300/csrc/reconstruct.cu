@@ -146,11 +146,10 @@ __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, cons
   }
 }
 
-// Matched-filter score s(t) = Re sum_{l=1}^{m} c_l w^l, w = e^{-i 2 pi t / T},
-// by complex Horner (4 FFMA per harmonic).
-__device__ __forceinline__ float mf_score(const float2* c, uint32_t m, const float2* s_tab, bool tl, uint32_t t) {
-  float2 w = phase(s_tab, t, tl);
-  w.y = -w.y;
+// Matched-filter score s(t) = Re sum_{l=1}^{m} c_l w^l for w = e^{-i 2 pi t / T},
+// by complex Horner (4 FFMA per harmonic). `we` is e^{+i 2 pi t / T}.
+__device__ __forceinline__ float mf_score(const float2* c, uint32_t m, float2 we) {
+  const float2 w = make_float2(we.x, -we.y);
   float ax = c[m - 1].x, ay = c[m - 1].y;
   for (int l = int(m) - 2; l >= 0; --l) {
     const float nx = fmaf(ax, w.x, fmaf(-ay, w.y, c[l].x));
@@ -174,18 +173,30 @@ __device__ __forceinline__ void mf_take(float s, uint32_t t, float& bs, uint32_t
   }
 }
 
+// Grid spacing of the branch and bound for a frame: the largest power of two
+// D <= 64 with w_m^2 D^2 / 8 <= 0.02, so that for every pixel the curvature
+// term M2 D^2 / 8 stays below 2% of M0 (M2 <= w_m^2 M0). G = ceil(T / D) is
+// then at most 1024.
+uint32_t mf_grid_spacing(uint32_t T, uint32_t m) {
+  const double w = 2.0 * M_PI * double(m) / double(T);
+  uint32_t D = 64u;
+  while (D > 1u && w * w * double(D) * double(D) / 8.0 > 0.02) D >>= 1;
+  return D;
+}
+
 // Exact argmax over integer t in [0, T) (smallest t on ties) of the FP32
 // scores, one warp per pixel, by branch and bound: s is a trigonometric
 // polynomial with |s''| <= M2 = sum_l |c_l| w_l^2, so on an interval of length
 // L between grid points s <= max(endpoints) + M2 L^2 / 8. Scores are evaluated
-// on a grid of spacing D (a power of two, M2 D^2 / 8 <= 0.02 M0,
-// M0 = sum_l |c_l|), and only intervals whose bound (plus a margin covering
-// the FP32 evaluation error of both ends) reaches the best grid score are
+// on the grid t = g D (phases from the conflict-free coarse table s_wg, scores
+// kept in s_grid), and only intervals whose bound (plus a margin covering the
+// FP32 evaluation error of both ends) reaches the best grid score are
 // evaluated point by point. Every t whose FP32 score can be the maximum is
-// evaluated with the same code as an exhaustive scan, so the result equals
-// the exhaustive FP32 argmax.
+// evaluated with the same arithmetic as an exhaustive scan, so the result
+// equals the exhaustive FP32 argmax.
 __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, uint32_t T, const float2* s_tab,
-                                                   bool tl, int excl_t, float min_sep, float* best_s,
+                                                   bool tl, const float2* s_wg, float* s_grid, uint32_t D,
+                                                   uint32_t G, int excl_t, float min_sep, float* best_s,
                                                    uint32_t* best_t) {
   const uint32_t lane = threadIdx.x & 31u;
   float m0 = 0.f, m2 = 0.f;
@@ -214,18 +225,16 @@ __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, 
     return;
   }
   m2 *= 1.01f;
-  uint32_t D = 64u;
-  while (D > 1u && m2 * float(D * D) * 0.125f > 0.02f * m0) D >>= 1;
-  const uint32_t G = (T + D - 1u) / D;
   const float margin = 4e-5f * m0 + 1e-30f;
   float bs = -FLT_MAX;
   uint32_t bt = 0xffffffffu;
-  // grid points
+  // grid points (every score kept: the interval bounds need them)
   for (uint32_t g = lane; g < G; g += 32u) {
-    const uint32_t t = g * D;
-    if (!mf_allowed(t, excl_t, min_sep, T)) continue;
-    mf_take(mf_score(c, m, s_tab, tl, t), t, bs, bt);
+    const float sg = mf_score(c, m, s_wg[g]);
+    s_grid[g] = sg;
+    if (mf_allowed(g * D, excl_t, min_sep, T)) mf_take(sg, g * D, bs, bt);
   }
+  __syncwarp();
   float best_grid = bs;
   for (int off = 16; off; off >>= 1) best_grid = fmaxf(best_grid, __shfl_xor_sync(0xffffffffu, best_grid, off));
   // intervals whose bound reaches the best grid score
@@ -234,11 +243,9 @@ __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, 
       const uint32_t i = base + lane;
       bool surv = false;
       if (i < G) {
-        const uint32_t a = i * D;
-        const uint32_t len = min(D, T - a);
+        const uint32_t len = min(D, T - i * D);
         if (len > 1u) {
-          const float sa = mf_score(c, m, s_tab, tl, a);
-          const float sb = mf_score(c, m, s_tab, tl, (a + len) % T);
+          const float sa = s_grid[i], sb = s_grid[i + 1u < G ? i + 1u : 0u];
           surv = fmaxf(sa, sb) + m2 * float(len * len) * 0.125f + margin >= best_grid;
         }
       }
@@ -250,11 +257,12 @@ __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, 
         const uint32_t len = min(D, T - a);
         for (uint32_t t = a + 1u + lane; t < a + len; t += 32u) {
           if (!mf_allowed(t, excl_t, min_sep, T)) continue;
-          mf_take(mf_score(c, m, s_tab, tl, t), t, bs, bt);
+          mf_take(mf_score(c, m, phase(s_tab, t, tl)), t, bs, bt);
         }
       }
     }
   }
+  __syncwarp();
   for (int off = 16; off; off >>= 1) {
     const float os = __shfl_xor_sync(0xffffffffu, bs, off);
     const uint32_t ot = __shfl_xor_sync(0xffffffffu, bt, off);
@@ -264,26 +272,35 @@ __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, 
   *best_t = bt;
 }
 
-// Matched-filter initialisation, one warp per pixel.
+// Matched-filter initialisation, one warp per pixel. Dynamic shared memory:
+// the phase table, the coarse table e^{i 2 pi g D / T} (G entries) and one
+// row of G grid scores per warp.
 template <int K>
 __global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
                                                  uint32_t P, uint32_t T, uint32_t m,
                                                  const float2* __restrict__ table, uint32_t entries,
-                                                 int two_level, const float2* __restrict__ hh_g,
+                                                 int two_level, uint32_t D, const float2* __restrict__ hh_g,
                                                  const float* __restrict__ misc, float prune_alpha, float min_sep,
                                                  float* __restrict__ depth, float* __restrict__ alpha,
                                                  uint8_t* __restrict__ active, float* __restrict__ alpha0) {
   extern __shared__ float2 s_tab[];
   __shared__ float2 s_c[kBlock / 32][kMaxM];
   __shared__ float2 s_hh[kMaxM];
+  const uint32_t G = (T + D - 1u) / D;
+  float2* s_wg = s_tab + entries;
+  float* s_grid_all = reinterpret_cast<float*>(s_wg + G);
   if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
-  load_table(s_tab, table, entries);
   const bool tl = two_level != 0;
+  for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_tab[i] = table[i];
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * D, tl);
+  __syncthreads();
   const float invT = 1.0f / float(T);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   const float E2 = misc[MISC_E2];
   float2* c = s_c[warp];
+  float* s_grid = s_grid_all + warp * G;
   for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb) {
     const uint32_t cnt = n[p];
     if (lane < m) {
@@ -294,7 +311,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, c
     __syncwarp();
     float s1;
     uint32_t t1;
-    warp_argmax_scores(c, m, T, s_tab, tl, -1, 0.f, &s1, &t1);
+    warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, -1, 0.f, &s1, &t1);
     if (t1 >= T) {  // no finite score (cannot happen for finite z)
       t1 = 0u;
       s1 = 0.f;
@@ -318,7 +335,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, c
       __syncwarp();
       float s2;
       uint32_t t2;
-      warp_argmax_scores(c, m, T, s_tab, tl, int(t1), min_sep, &s2, &t2);
+      warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, int(t1), min_sep, &s2, &t2);
       if (t2 >= T) {
         t2 = 0u;
         s2 = 0.f;
@@ -372,6 +389,7 @@ __device__ __forceinline__ void grad_pixel(const float2* __restrict__ zp, uint32
 #pragma unroll
   for (int k = 0; k < K; ++k) gt[k] = ga[k] = 0.f;
   const float wstep = 6.283185307179586f / Tf;
+#pragma unroll 4
   for (uint32_t l = 0; l < m; ++l) {
     const float2 hv = s_hh[l];
     const float2 zl = zp[l];
@@ -511,8 +529,15 @@ __device__ __forceinline__ float sphere_depth(const Stencil& st, float tq, int c
 // read from and written to global memory once.
 constexpr int kTW = 16, kTH = 16;
 
+// One thread per pixel of the post-gradient region (tile + 2R halo), rounded
+// up to whole warps, so that every stage runs in a single round.
+template <int R>
+__host__ __device__ constexpr int iter_threads() {
+  return (((kTW + 4 * R) * (kTH + 4 * R) + 31) / 32) * 32;
+}
+
 template <int K, int R>
-__global__ void __launch_bounds__(kTW* kTH) k_iter(Stencil st, const float2* __restrict__ z,
+__global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const float2* __restrict__ z,
                                                    const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
                                                    const float2* __restrict__ hh_g, const float* __restrict__ misc,
                                                    float* depth, float* alpha, uint8_t* active, float* alpha0) {
@@ -531,7 +556,8 @@ __global__ void __launch_bounds__(kTW* kTH) k_iter(Stencil st, const float2* __r
   const float nmax = misc[MISC_NMAX];
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   // 1) gradient step on the region (pixels outside the array are inactive)
-  for (int i = tid; i < RH * RW; i += kTW * kTH) {
+  constexpr int NT = iter_threads<R>();
+  for (int i = tid; i < RH * RW; i += NT) {
     const int rr = r0 - H + i / RW, cc = c0 - H + i % RW;
     float t[K], a[K];
     bool act[K];
@@ -561,7 +587,7 @@ __global__ void __launch_bounds__(kTW* kTH) k_iter(Stencil st, const float2* __r
   }
   __syncthreads();
   // 2) normals on the tile plus an R halo
-  for (int i = tid; i < NH * NW; i += kTW * kTH) {
+  for (int i = tid; i < NH * NW; i += NT) {
     const int lr = i / NW + R, lc = i % NW + R;  // region coordinates
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -602,6 +628,7 @@ __global__ void __launch_bounds__(kTW* kTH) k_iter(Stencil st, const float2* __r
   }
   __syncthreads();
   // 3) sphere projection, smoothing and pruning on the tile
+  if (tid >= kTW * kTH) return;
   const int ty = tid / kTW, tx = tid % kTW;
   const int rr = r0 + ty, cc = c0 + tx;
   if (rr >= int(st.rows) || cc >= int(st.cols)) return;
@@ -688,10 +715,8 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   const uint32_t P = rows * cols;
   const size_t tab_smem = size_t(tab.entries) * sizeof(float2);
   const int tl = tab.two_level ? 1 : 0;
-  if (tab_smem > 48 * 1024) {
+  if (tab_smem > 48 * 1024)
     SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
-    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
-  }
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
     k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
@@ -699,16 +724,22 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   if (prm.init_mode == SRT3D_INIT_MATCHED) {
+    const uint32_t D = mf_grid_spacing(T, m);
+    const uint32_t G = (T + D - 1u) / D;
+    const size_t init_smem = tab_smem + size_t(G) * sizeof(float2) + size_t(kBlock / 32) * G * sizeof(float);
+    if (init_smem > 48 * 1024)
+      SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               int(init_smem)));
     int bps = 0;
-    SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init<K>, kBlock, tab_smem));
+    SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init<K>, kBlock, init_smem));
     if (bps < 1) bps = 1;
     const uint32_t wpb = kBlock / 32;
     const uint64_t need = (uint64_t(P) + wpb - 1) / wpb;
     const uint32_t grid = uint32_t(std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps));
     {
       const ProfMark mk = prof_begin(ctx, KID_INIT, stream);
-      k_init<K><<<grid, kBlock, tab_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, sc.hh, sc.misc,
-                                                  prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
+      k_init<K><<<grid, kBlock, init_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, D, sc.hh, sc.misc,
+                                                   prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
       prof_end(ctx, KID_INIT, mk, stream);
     }
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
@@ -737,11 +768,11 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     if (!prm.regularize) {
       k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     } else if (prm.radius == 1) {
-      k_iter<K, 1><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     } else if (prm.radius == 2) {
-      k_iter<K, 2><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 2><<<tiles, iter_threads<2>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     } else {
-      k_iter<K, 3><<<tiles, kTW * kTH, 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 3><<<tiles, iter_threads<3>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     }
     prof_end(ctx, prm.regularize ? KID_ITER : KID_GRAD, mk, stream);
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
