@@ -1,0 +1,102 @@
+"""GPU parity of the tensor-core histogram sketch (tcgen05, Sec. 2 Eqs. 2-3)
+against the FP64 oracle. FP16 hi+lo split: <= 1e-4 in normalised units (each
+summand of Eq. 3 has modulus 1) and counts bit-exact; BF16: counts exact, the
+error is reported and bounded loosely (the BF16 Fourier factors carry 8 bits)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2203_00952_gb300 import binding as B
+from paper_2203_00952_gb300 import synth
+
+from gpu_util import counts, ctx, dev_hist, sketch_err, to_complex  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+SPLIT_TOL = 1e-4
+BF16_TOL = 2e-2
+
+
+def run(ctx, y, m, precision):
+    P, T = y.shape
+    S = torch.full((P, m, 2), float("nan"), device="cuda")
+    n = torch.zeros(P, dtype=torch.int32, device="cuda")
+    B.srt3d_sketch_hist(ctx, dev_hist(y), T, m, precision, S, n)
+    B.srt3d_sync(ctx)
+    return S, n
+
+
+@pytest.mark.parametrize("P,T,m", [(1, 64, 1), (127, 128, 4), (128, 1024, 10), (129, 64, 31), (260, 512, 16),
+                                   (300, 4096, 32), (513, 4096, 10)])
+def test_fp16_split_matches_oracle(ctx, P, T, m):
+    rng = np.random.default_rng(P + T + m)
+    y = rng.poisson(rng.uniform(0.2, 6.0, size=(P, 1)), size=(P, T)).astype(np.uint16)
+    S, n = run(ctx, y, m, B.SRT3D_FP16_SPLIT)
+    S_ref, n_ref = oracle.sketch_hist(y, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= SPLIT_TOL
+
+
+def test_fp16_split_exact_for_counts_above_2048(ctx):
+    # counts > 2048 are split exactly into (y & ~31) + (y & 31)
+    P, T, m = 200, 256, 8
+    rng = np.random.default_rng(9)
+    y = rng.integers(0, 3, size=(P, T)).astype(np.uint16)
+    y[0, 5] = 2048
+    y[1, 7] = 2049
+    y[2, 0] = 65535
+    y[3, :] = 40000
+    y[150, 200] = 3000
+    S, n = run(ctx, y, m, B.SRT3D_FP16_SPLIT)
+    S_ref, n_ref = oracle.sketch_hist(y, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= SPLIT_TOL
+
+
+@pytest.mark.parametrize("P,T,m", [(1, 64, 1), (130, 1024, 10), (300, 4096, 32)])
+def test_bf16_reported_error(ctx, P, T, m):
+    rng = np.random.default_rng(P * 3 + m)
+    y = rng.poisson(rng.uniform(0.2, 6.0, size=(P, 1)), size=(P, T)).astype(np.uint16)
+    S, n = run(ctx, y, m, B.SRT3D_BF16)
+    S_ref, n_ref = oracle.sketch_hist(y, m)
+    assert np.array_equal(counts(n), n_ref)
+    err = sketch_err(S, n, S_ref, n_ref)
+    print(f"BF16 sketch error (normalised) P={P} T={T} m={m}: {err:.3e}")
+    assert err <= BF16_TOL
+
+
+def test_tc_argument_checks(ctx):
+    y = np.zeros((4, 100), np.uint16)  # T not a multiple of 64
+    S = torch.zeros(4, 4, 2, device="cuda")
+    n = torch.zeros(4, dtype=torch.int32, device="cuda")
+    with pytest.raises(B.SRT3DError) as ei:
+        B.srt3d_sketch_hist(ctx, dev_hist(y), 100, 4, B.SRT3D_FP16_SPLIT, S, n)
+    assert ei.value.status == B.SRT3D_EINVAL
+
+
+def test_full_size_512x512_histograms_sampled(ctx):
+    # The histogram workload at full size (512x512 x 4096 bins, 10 000
+    # counts/pixel, SBR 0.2, m = 32): every precision on the whole frame, the
+    # oracle on a sample of pixels.
+    spec = synth.frame_512x512_hist()
+    m = 32
+    hist, _ = synth.make_hist_frame_torch(spec, synth.SEED_512x512)
+    P, T = spec.num_pixels, spec.T
+    rng = np.random.default_rng(12)
+    pix = np.unique(np.concatenate([rng.choice(P, 96, replace=False), [0, P - 1]]))
+    y_s = hist[torch.from_numpy(pix).cuda()].cpu().numpy().view(np.uint16)
+    S_ref, n_ref = oracle.sketch_hist(y_s, m)
+    for prec, tol in ((B.SRT3D_FP32, 1e-5), (B.SRT3D_FP16_SPLIT, SPLIT_TOL), (B.SRT3D_BF16, BF16_TOL)):
+        S = torch.empty(P, m, 2, device="cuda")
+        n = torch.empty(P, dtype=torch.int32, device="cuda")
+        B.srt3d_sketch_hist(ctx, hist, T, m, prec, S, n)
+        B.srt3d_sync(ctx)
+        Sg = to_complex(S)[pix]
+        assert np.array_equal(counts(n)[pix], n_ref)
+        err = np.max(np.abs(Sg - S_ref) / n_ref[:, None])
+        print(f"precision {prec}: max normalised error {err:.3e}")
+        assert err <= tol
+        del S, n
+    del hist
+    torch.cuda.empty_cache()
