@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hist-steps", type=int, default=10)
+    ap.add_argument("--only", choices=["all", "step", "hist"], default="all")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -186,6 +188,62 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+# ----------------------------------------------------------------- histogram path
+
+HIST_M = 32
+
+
+def hist_section(B, ctx, dev, steps, flush):
+    """Histogram sketch of the 512x512 x 4096-bin workload (10 000 counts/px,
+    SBR 0.2, m = 32) in every precision: device time per launch (CUDA events,
+    L2 evicted between launches), HBM roofline, tensor throughput, and the
+    error against the FP64 oracle on sampled pixels."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2203_00952_gb300 import synth
+
+    spec = synth.frame_512x512_hist()
+    hist, _ = synth.make_hist_frame_torch(spec, synth.SEED_512x512, device=dev)
+    P, T, m = spec.num_pixels, spec.T, HIST_M
+    S = torch.empty(P, m, 2, device=dev)
+    n = torch.empty(P, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(5)
+    pix = np.sort(rng.choice(P, 32, replace=False))
+    y_s = hist[torch.from_numpy(pix).to(dev)].cpu().numpy().view(np.uint16)
+    S_ref, n_ref = oracle.sketch_hist(y_s, m)
+    hbm_peak, peak_kind = load_peaks()
+    out = {"workload": "hist_512x512_T4096_m32", "photon_equivalents_per_frame": int(n_ref.mean() * P)}
+    names = {B.SRT3D_FP32: "fp32", B.SRT3D_FP16_SPLIT: "fp16_split", B.SRT3D_BF16: "bf16"}
+    for prec in (B.SRT3D_FP16_SPLIT, B.SRT3D_BF16, B.SRT3D_FP32):
+        for _ in range(2):
+            B.srt3d_sketch_hist(ctx, hist, T, m, prec, S, n, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            B.srt3d_sketch_hist(ctx, hist, T, m, prec, S, n, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        B.srt3d_sync(ctx, stream)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        alg_bytes = P * T * 2 + P * m * 8 + P * 4
+        nn = 2 * ((2 * m + 15) // 16) * 16 if prec == B.SRT3D_FP16_SPLIT else ((2 * m + 15) // 16) * 16
+        err = float(np.max(np.abs(np.asarray(S.cpu()).view(np.complex64)[pix, :, 0] - S_ref) / n_ref[:, None]))
+        ach = alg_bytes / (ms / 1e3) / 1e9
+        out[names[prec]] = {"ms": ms, "GB_per_s": ach, "hbm_frac": ach / hbm_peak,
+                            "tensor_tflops": (2.0 * P * T * nn / (ms / 1e3) / 1e12) if prec else None,
+                            "photons_per_s": float(n_ref.mean() * P / (ms / 1e3)),
+                            "max_err_normalised": err}
+    out["hbm_peak_gbs"] = hbm_peak
+    out["peak_source"] = f"MEASURED_PEAKS.json ({peak_kind})"
+    del hist, S, n
+    torch.cuda.empty_cache()
+    return out
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def load_peaks():
@@ -241,6 +299,15 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     builder.build()
+    if args.only == "hist":
+        # histogram path alone (for profiling): no step timing, no baseline
+        ctx = B.srt3d_create(local)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        res = hist_section(B, ctx, dev, args.hist_steps, flush)
+        B.srt3d_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"hist_sketch": res}), flush=True)
+        return
     spec, prm = spec_and_params()
     m, K = WORKLOAD["m"], WORKLOAD["k_max"]
 
@@ -346,6 +413,9 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes
     d2h = sum(o.numel() * o.element_size() for o in out_host)
 
+    hist = None
+    if args.only in ("all", "hist") and rank == 0:
+        hist = hist_section(B, ctx, dev, args.hist_steps, flush)
     B.srt3d_destroy(ctx)
     if rank != 0:
         if world > 1:
@@ -409,6 +479,7 @@ def gpu_arm(args):
         "roofline": roofline,
         "rooflines": rooflines,
         "cpu_baseline": cpu,
+        "hist_sketch": hist,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

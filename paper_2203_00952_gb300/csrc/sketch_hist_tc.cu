@@ -2,18 +2,18 @@
 //   Z[P x N] = Y[P x T] F^T[N x T]^T, F^T[2(l-1)][b] = cos(2 pi ((l b) mod T) / T),
 //   F^T[2(l-1)+1][b] = sin(...), N = 2m rounded up to 16 (x2 for the split).
 //
-// Persistent, warp-specialised CTA (384 threads, one per SM), M = 128 pixels
+// Persistent, warp-specialised CTA (512 threads, one per SM), M = 128 pixels
 // per tile, K = 64 bins per pipeline stage:
-//   warp 0     TMA producer: Y tile [128 x 64] u16 and F^T tile [N x 64],
-//              both 128-byte swizzled (the canonical K-major operand layout)
-//   warps 4-7  converters: each thread owns one pixel row of the stage and
-//              converts it in place to FP16 (exact for counts <= 2048; larger
-//              counts are split exactly into (y & ~31) in A and (y & 31) in a
-//              second operand A2) or to BF16; they also count the row's
-//              photons (n) in integers
-//   warp 1     MMA issuer: tcgen05.mma.kind::f16 into a double-buffered FP32
-//              accumulator in TMEM; A2 only for stages that hold a count > 2048
-//   warps 8-11 epilogue: tcgen05.ld of the accumulator, hi + lo, store S
+//   warp 0      TMA producer: Y tile [128 x 64] u16 and F^T tile [N x 64],
+//               both 128-byte swizzled (the canonical K-major operand layout)
+//   warps 4-11  converters: two threads per pixel row convert the stage in
+//               place to FP16 (exact for counts <= 2048; larger counts are
+//               split exactly into (y & ~31) in A and (y & 31) in a second
+//               operand A2) or to BF16; they also count the row's photons (n)
+//               in integers
+//   warp 1      MMA issuer: tcgen05.mma.kind::f16 into a double-buffered FP32
+//               accumulator in TMEM; A2 only for stages that hold a count > 2048
+//   warps 12-15 epilogue: tcgen05.ld of the accumulator, hi + lo, store S
 // SRT3D_FP16_SPLIT uses F = F_hi + F_lo (both FP16, stacked along N, one MMA
 // computes both products); SRT3D_BF16 uses a single BF16 F and BF16 counts.
 // Every mbarrier wait is bounded: on timeout the kernel latches an error flag,
@@ -32,7 +32,7 @@ namespace srt3d {
 
 namespace {
 
-constexpr int kThreads = 384;
+constexpr int kThreads = 512;
 constexpr int kTileM = 128;
 constexpr int kTileK = 64;  // bins per stage: 64 x 2 B = one 128-byte swizzle row
 constexpr uint32_t kABytes = kTileM * kTileK * 2;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&conv[s]), 128);
+      mbar_init(smem_u32(&conv[s]), 256);
       mbar_init(smem_u32(&empty[s]), 1);
       split_gen[s] = 0xffffffffu;
     }
@@ -279,9 +279,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       while (!mbar_try_wait(smem_u32(drain), 0u) && clock64() - t0 < kWaitCycles) {
       }
     }
-  } else if (warp >= 4 && warp < 8) {
+  } else if (warp >= 4 && warp < 12) {
     // ---------------------------------------------------------------- converters
-    const uint32_t row = threadIdx.x - 128u;
+    // 256 threads: thread (half, row) owns four 16-byte chunks of one pixel
+    // row (128 bytes) of every stage. Chunks are visited in swizzled order
+    // (c ^ (row & 7)) so the 32 rows of a warp cover all banks; the conversion
+    // is elementwise, so the order does not matter. Small counts take an exact
+    // bit-pattern path (FP16: (0x6400 | y) - 1024 for y < 1024; BF16:
+    // (0x4300 | y) - 128 for y < 128); others take the rounding conversion.
+    // A2 (FP16 split) starts zeroed and a thread rewrites its A2 chunks only
+    // while they hold, or last held, a count above 2048.
+    const uint32_t ct = threadIdx.x - 128u;
+    const uint32_t row = ct & 127u, c0 = (ct >> 7) * 4u;
+    const uint32_t sw = row & 7u;
+    uint32_t dirty = 0u;  // bit s: this thread's A2 chunks of stage slot s are nonzero
+    if (kSplit) {
+      for (int s2 = 0; s2 < ST; ++s2) {
+        uint8_t* ra2 = sA2(s2) + row * 128u;
+#pragma unroll
+        for (uint32_t c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4*>(ra2 + (((c0 + c) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      fence_proxy_async_smem();
+    }
+    constexpr uint32_t kMagicLimit = kSplit ? 0x03FF03FFu : 0x007F007Fu;
     uint32_t it = 0;
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -289,46 +310,89 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
         const uint32_t s = it % ST, ph = (it / ST) & 1u;
         if (!(ok = mbar_wait(smem_u32(&full[s]), ph, abort_flag, gflags))) break;
-        uint4* ra = reinterpret_cast<uint4*>(sA(s) + row * 128u);
-        uint4* ra2 = reinterpret_cast<uint4*>(sA2(s) + row * 128u);
-        bool large = false;
+        uint8_t* ra = sA(s) + row * 128u;
+        uint8_t* ra2 = sA2(s) + row * 128u;
+        uint32_t w[16];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint4 v = ra[c];
-          uint32_t w[4] = {v.x, v.y, v.z, v.w};
-          uint32_t hi[4], lo[4];
+        for (uint32_t c = 0; c < 4; ++c) {
+          const uint4 v = *reinterpret_cast<const uint4*>(ra + (((c0 + c) ^ sw) << 4));
+          w[4 * c] = v.x;
+          w[4 * c + 1] = v.y;
+          w[4 * c + 2] = v.z;
+          w[4 * c + 3] = v.w;
+        }
+        uint32_t over = 0u, big = 0u;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t y0 = w[q] & 0xffffu, y1 = w[q] >> 16;
-            cnt += y0 + y1;
+        for (int q = 0; q < 16; ++q) {
+          cnt = __dp2a_lo(w[q], 0x00000101u, cnt);  // + low half + high half
+          over |= __vcmpgtu2(w[q], kMagicLimit);
+          if (kSplit) big |= __vcmpgtu2(w[q], 0x08000800u);
+        }
+        uint32_t hi[16], lo[16];
+        if (over == 0u) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
             if (kSplit) {
-              const bool big0 = y0 > 2048u, big1 = y1 > 2048u;
-              large |= big0 | big1;
-              const __half h0 = __uint2half_rn(big0 ? (y0 & ~31u) : y0);
-              const __half h1 = __uint2half_rn(big1 ? (y1 & ~31u) : y1);
-              const __half l0 = __uint2half_rn(big0 ? (y0 & 31u) : 0u);
-              const __half l1 = __uint2half_rn(big1 ? (y1 & 31u) : 0u);
-              hi[q] = uint32_t(__half_as_ushort(h0)) | (uint32_t(__half_as_ushort(h1)) << 16);
-              lo[q] = uint32_t(__half_as_ushort(l0)) | (uint32_t(__half_as_ushort(l1)) << 16);
+              __half2 h = __halves2half2(__ushort_as_half(0), __ushort_as_half(0));
+              const uint32_t bits = w[q] | 0x64006400u;
+              memcpy(&h, &bits, 4);
+              h = __hsub2(h, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+              memcpy(&hi[q], &h, 4);
             } else {
-              const __nv_bfloat16 b0 = __uint2bfloat16_rn(y0);
-              const __nv_bfloat16 b1 = __uint2bfloat16_rn(y1);
-              hi[q] = uint32_t(__bfloat16_as_ushort(b0)) | (uint32_t(__bfloat16_as_ushort(b1)) << 16);
+              __nv_bfloat162 h;
+              const uint32_t bits = w[q] | 0x43004300u;
+              memcpy(&h, &bits, 4);
+              h = __hsub2(h, __halves2bfloat162(__ushort_as_bfloat16(0x4300), __ushort_as_bfloat16(0x4300)));
+              memcpy(&hi[q], &h, 4);
+            }
+            lo[q] = 0u;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            uint32_t y0 = w[q] & 0xffffu, y1 = w[q] >> 16;
+            if (kSplit) {
+              uint32_t l0 = 0u, l1 = 0u;
+              if (y0 > 2048u) {
+                l0 = y0 & 31u;
+                y0 &= ~31u;
+              }
+              if (y1 > 2048u) {
+                l1 = y1 & 31u;
+                y1 &= ~31u;
+              }
+              hi[q] = uint32_t(__half_as_ushort(__uint2half_rn(y0))) |
+                      (uint32_t(__half_as_ushort(__uint2half_rn(y1))) << 16);
+              lo[q] = uint32_t(__half_as_ushort(__uint2half_rn(l0))) |
+                      (uint32_t(__half_as_ushort(__uint2half_rn(l1))) << 16);
+            } else {
+              hi[q] = uint32_t(__bfloat16_as_ushort(__uint2bfloat16_rn(y0))) |
+                      (uint32_t(__bfloat16_as_ushort(__uint2bfloat16_rn(y1))) << 16);
               lo[q] = 0u;
             }
           }
-          ra[c] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          if (kSplit) ra2[c] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
-        if (kSplit && large) split_gen[s] = it;
+        const bool large = kSplit && big != 0u;
+        const bool rewrite_a2 = kSplit && (large || ((dirty >> s) & 1u));
+#pragma unroll
+        for (uint32_t c = 0; c < 4; ++c) {
+          const uint32_t off = ((c0 + c) ^ sw) << 4;
+          *reinterpret_cast<uint4*>(ra + off) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+          if (rewrite_a2)
+            *reinterpret_cast<uint4*>(ra2 + off) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
+        }
+        if (kSplit) {
+          dirty = large ? (dirty | (1u << s)) : (dirty & ~(1u << s));
+          if (large) split_gen[s] = it;
+        }
         fence_proxy_async_smem();
         mbar_arrive(smem_u32(&conv[s]));
       }
       if (!ok) break;
       const uint32_t p = tile * kTileM + row;
-      if (p < P) n[p] = cnt;
+      if (p < P) atomicAdd(n + p, cnt);  // two halves per row; n was zeroed before the launch
     }
-  } else if (warp >= 8) {
+  } else if (warp >= 12) {
     // ---------------------------------------------------------------- epilogue
     const uint32_t q = warp & 3u;  // TMEM lane quadrant of this warp
     const uint32_t acc_cols = ncols_alloc / 2;
@@ -469,6 +533,7 @@ srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const uint32_t ntiles = (P + kTileM - 1) / kTileM;
   const uint32_t grid = std::min<uint32_t>(ntiles, uint32_t(ctx->num_sms));
+  SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(n, 0, size_t(P) * sizeof(uint32_t), stream));
   const ProfMark mk = prof_begin(ctx, KID_SKETCH_HIST_TC, stream);
   kfn<<<grid, kThreads, smem, stream>>>(mapY, mapF, P, T, m, N2, ncols_alloc, S, n, ctx->d_flags);
   prof_end(ctx, KID_SKETCH_HIST_TC, mk, stream);
