@@ -101,7 +101,8 @@ srt3d_status grow(srt3d_ctx* ctx, DevBuf* buf, size_t bytes);
 // Launchers (no argument validation; callers validate).
 srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                   uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m,
-                                  int accumulate, float2* S, uint32_t* n, cudaStream_t stream);
+                                  int accumulate, float2* S, uint32_t* n, cudaStream_t stream,
+                                  uint32_t* flags = nullptr);
 srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n, uint32_t P,
                              uint32_t m, float2* z, cudaStream_t stream);
 srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_hist_from_stream(const uint16_t* __r
 
 srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                   uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int accumulate,
-                                  float2* S, uint32_t* n, cudaStream_t stream) {
+                                  float2* S, uint32_t* n, cudaStream_t stream, uint32_t* flags) {
   PhaseTable tab;
   srt3d_status st = get_phase_table(ctx, T, &tab);
   if (st != SRT3D_OK) return st;
@@ -235,7 +235,7 @@ srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const 
   const ProfMark mk = prof_begin(ctx, KID_SKETCH_STREAM, stream);
   fn<<<dim3(uint32_t(grid)), dim3(kBlock), smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, m, glog2,
                                                           accumulate, tab.dev, tab.entries, tab.two_level ? 1 : 0,
-                                                          S, n, ctx->d_flags);
+                                                          S, n, flags ? flags : ctx->d_flags);
   prof_end(ctx, KID_SKETCH_STREAM, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
