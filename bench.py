@@ -46,7 +46,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
-    ap.add_argument("--only", choices=["all", "step", "hist"], default="all")
+    ap.add_argument("--only", choices=["all", "step", "hist", "serving"], default="all")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -244,6 +245,146 @@ def hist_section(B, ctx, dev, steps, flush):
     return out
 
 
+# ----------------------------------------------------------------- serving
+
+SERVE = dict(sizes=(128, 256, 512), T=2048, m=16, sigma=4.0, nbar=(50.0, 2000.0), sbr=1.0, chunks=8, iters=25,
+             rate=300.0)
+
+
+def chunk_split(stamps, offsets, nchunks):
+    """Split every pixel's photons into `nchunks` consecutive runs (arrival
+    order); returns a list of (stamps, offsets) numpy arrays."""
+    import numpy as np
+
+    off = offsets.astype(np.int64)
+    cnt = np.diff(off)
+    out = []
+    for k in range(nchunks):
+        a = off[:-1] + (k * cnt) // nchunks
+        b = off[:-1] + ((k + 1) * cnt) // nchunks
+        ln = b - a
+        o = np.zeros(len(cnt) + 1, np.uint32)
+        np.cumsum(ln, out=o[1:])
+        idx = np.repeat(a - o[:-1].astype(np.int64), ln) + np.arange(int(o[-1]))
+        out.append((stamps[idx], o))
+    return out
+
+
+def serving_section(B, dev, seconds):
+    """Frames arrive as a Poisson process; each frame's photons come in 8
+    chunks spread over 1/300 s (host pinned buffers) and are sketched online
+    on the device; the last chunk starts the reconstruction; results are
+    polled back to host memory. Reports latency from the last chunk to the
+    result (and from the first chunk), and the sustained photon rate."""
+    import heapq
+
+    import numpy as np
+    import torch
+
+    from paper_2203_00952_gb300 import synth
+
+    cfg = SERVE
+    rng = np.random.default_rng(synth.SEED_SERVE)
+    pool = []
+    for i, n in enumerate(cfg["sizes"]):
+        for nbar in (150.0, 800.0):  # two photon levels per size inside the log-uniform range
+            spec = synth.FrameSpec(rows=n, cols=n, T=cfg["T"], sigma=cfg["sigma"], mean_photons=nbar,
+                                   sbr=cfg["sbr"], two_surface_frac=0.1)
+            fr = synth.make_stream_frame(spec, synth.SEED_SERVE, len(pool))
+            ch = []
+            for st, off in chunk_split(fr.stamps, fr.offsets, cfg["chunks"]):
+                st_p = torch.from_numpy(st.view(np.int16)).pin_memory().numpy().view(np.uint16)
+                off_p = torch.from_numpy(off.view(np.int32)).pin_memory().numpy().view(np.uint32)
+                ch.append((st_p, off_p))
+            pool.append((spec, ch, int(fr.offsets[-1])))
+    h = {cfg["sigma"]: synth.impulse_response(cfg["T"], cfg["sigma"]).astype(np.float32)}
+    prm = B.make_params(iters=cfg["iters"], k_max=2, d_max=6 * cfg["sigma"], min_sep=3 * cfg["sigma"])
+    ctx = B.srt3d_create(int(dev.index or 0))
+    outbuf = {}
+
+    def out_for(spec):
+        key = (spec.rows, spec.cols)
+        if key not in outbuf:
+            P = spec.num_pixels
+            outbuf[key] = (np.zeros((P, 2), np.float32), np.zeros((P, 2), np.float32), np.zeros((P, 2), np.uint8),
+                           np.zeros(P, np.float32), None)
+        return outbuf[key]
+
+    # warm-up: one frame of each pool entry
+    for j, (spec, ch, _) in enumerate(pool):
+        for k, (st, off) in enumerate(ch):
+            B.srt3d_submit(ctx, 10**9 + j, spec.rows, spec.cols, spec.T, cfg["m"], h[cfg["sigma"]], prm, st, off,
+                           int(k == len(ch) - 1))
+        B.srt3d_poll(ctx, 10**9 + j, 60_000_000, *out_for(spec))
+    arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate"], size=int(seconds * cfg["rate"] * 1.5) + 8))
+    arrivals = arrivals[arrivals < seconds]
+    choice = rng.integers(0, len(pool), size=len(arrivals))
+    # chunk k of frame i is due at arrival_i + k / (rate * chunks); chunk k+1
+    # is scheduled only once chunk k has been accepted
+    events = [(float(t), i, 0) for i, t in enumerate(arrivals)]
+    heapq.heapify(events)
+    t0 = time.perf_counter()
+    deadline = seconds + 120.0
+    first_at, last_at, lat_last, lat_first, photons = {}, {}, [], [], 0
+    inflight = []
+    busy_retries = 0
+    while events or inflight:
+        now = time.perf_counter() - t0
+        if now > deadline:
+            raise RuntimeError(f"serving run exceeded {deadline:.0f} s ({len(inflight)} frames in flight)")
+        if events and events[0][0] <= now:
+            t, i, k = heapq.heappop(events)
+            spec, ch, nph = pool[choice[i]]
+            st, off = ch[k]
+            rc = B.srt3d_submit(ctx, i, spec.rows, spec.cols, spec.T, cfg["m"], h[cfg["sigma"]], prm, st, off,
+                                int(k == cfg["chunks"] - 1), check=False)
+            if rc == B.SRT3D_EBUSY:
+                busy_retries += 1
+                heapq.heappush(events, (now + 2e-4, i, k))
+            elif rc != B.SRT3D_OK:
+                raise RuntimeError(f"srt3d_submit failed: {rc}")
+            else:
+                if k == 0:
+                    first_at[i] = time.perf_counter()
+                if k == cfg["chunks"] - 1:
+                    last_at[i] = time.perf_counter()
+                    inflight.append(i)
+                else:
+                    due = float(arrivals[i]) + (k + 1) / (cfg["rate"] * cfg["chunks"])
+                    heapq.heappush(events, (max(due, now), i, k + 1))
+        # poll every frame in flight without waiting
+        progressed = False
+        for i in list(inflight):
+            spec, ch, nph = pool[choice[i]]
+            rc = B.srt3d_poll(ctx, i, 0, *out_for(spec), check=False)
+            if rc == B.SRT3D_OK:
+                tnow = time.perf_counter()
+                lat_last.append(tnow - last_at[i])
+                lat_first.append(tnow - first_at[i])
+                photons += nph
+                inflight.remove(i)
+                progressed = True
+            elif rc != B.SRT3D_ETIMEDOUT:
+                raise RuntimeError(f"srt3d_poll failed: {rc}")
+        if not progressed and events:
+            wait = events[0][0] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 2e-4))
+    wall = time.perf_counter() - t0
+    B.srt3d_destroy(ctx)
+    lat_last = np.array(lat_last) * 1e3
+    lat_first = np.array(lat_first) * 1e3
+    return {"workload": "serving_poisson300_T2048_m16_K2_it25_8chunks", "seconds_offered": seconds,
+            "frames": int(len(lat_last)), "photons_per_s": photons / wall, "frames_per_s": len(lat_last) / wall,
+            "latency_last_chunk_ms": {"p50": float(np.percentile(lat_last, 50)),
+                                      "p99": float(np.percentile(lat_last, 99))},
+            "latency_first_chunk_ms": {"p50": float(np.percentile(lat_first, 50)),
+                                       "p99": float(np.percentile(lat_first, 99))},
+            "admission_retries": busy_retries,
+            "pool": "6 frames: {128,256,512}^2 x {150, 800} photons/px, SBR 1, 10% two-surface; chunks from pinned "
+                    "host memory"}
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def load_peaks():
@@ -299,6 +440,11 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     builder.build()
+    if args.only == "serving":
+        res = serving_section(B, dev, args.serving_seconds)
+        if rank == 0:
+            print(json.dumps({"serving": res}), flush=True)
+        return
     if args.only == "hist":
         # histogram path alone (for profiling): no step timing, no baseline
         ctx = B.srt3d_create(local)
@@ -388,35 +534,35 @@ def gpu_arm(args):
     det = act[:, 0] & (err <= 3 * spec.sigma)
     dae = float(err[det].mean())
 
-    # end to end through the C-ABI with host buffers (pinned), copies inside
-    host_stamps = torch.from_numpy(fr.stamps.view(np.int16)).pin_memory()
-    host_offsets = torch.from_numpy(fr.offsets.view(np.int32)).pin_memory()
-    out_host = [torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (depth, alpha, active, alpha0)]
-    sd2 = torch.empty_like(stamps)
-    od2 = torch.empty_like(offsets)
-    z2 = torch.empty_like(z)
-    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.e2e_steps)]
+    # end to end through the public host-buffer API: srt3d_submit (pinned
+    # stamps and offsets, copied to the device inside) + srt3d_poll (results
+    # copied back to host memory)
+    host_stamps = torch.from_numpy(fr.stamps.view(np.int16)).pin_memory().numpy().view(np.uint16)
+    host_offsets = torch.from_numpy(fr.offsets.view(np.int32)).pin_memory().numpy().view(np.uint32)
+    h_host = synth.impulse_response(T, spec.sigma).astype(np.float32)
+    outs = (np.zeros((P, K), np.float32), np.zeros((P, K), np.float32), np.zeros((P, K), np.uint8),
+            np.zeros(P, np.float32), None)
+    e2e_ms = []
     for i in range(args.e2e_steps + 2):
-        flush.fill_(float(i))
+        t0 = time.perf_counter()
+        B.srt3d_submit(ctx, 1 + i, spec.rows, spec.cols, T, m, h_host, params, host_stamps, host_offsets, 1)
+        B.srt3d_poll(ctx, 1 + i, 60_000_000, *outs)
         if i >= 2:
-            e2e_ev[i - 2][0].record(stream)
-        sd2.copy_(host_stamps, non_blocking=True)
-        od2.copy_(host_offsets, non_blocking=True)
-        step(stream, sd2, od2, z2)
-        for o, x in zip(out_host, (depth, alpha, active, alpha0)):
-            o.copy_(x, non_blocking=True)
-        if i >= 2:
-            e2e_ev[i - 2][1].record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = float(np.mean([a.elapsed_time(b) for a, b in e2e_ev]))
-    h2d = fr.stamps.nbytes + fr.offsets.nbytes
-    d2h = sum(o.numel() * o.element_size() for o in out_host)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = float(np.median(e2e_ms))
+    h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
+    d2h = sum(o.nbytes for o in outs if o is not None)
 
     hist = None
     if args.only in ("all", "hist") and rank == 0:
         hist = hist_section(B, ctx, dev, args.hist_steps, flush)
     B.srt3d_destroy(ctx)
+    serving = None
+    if args.only == "all" and rank == 0 and world == 1:
+        try:
+            serving = serving_section(B, dev, args.serving_seconds)
+        except Exception as exc:  # the main line must still print
+            serving = {"error": repr(exc)[:300]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -474,12 +620,14 @@ def gpu_arm(args):
         "wall_s": wall,
         "clocks": clocks.summary(),
         "e2e": {"value": world * N / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "api": "srt3d_submit (pinned host stamps/offsets) + srt3d_poll (host results), host wall clock"},
         "gpu_launches": int(sum(v[1] for v in prof.values())),
         "roofline": roofline,
         "rooflines": rooflines,
         "cpu_baseline": cpu,
         "hist_sketch": hist,
+        "serving": serving,
     }
     print(json.dumps(out), flush=True)
     if world > 1:

@@ -30,14 +30,21 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 struct Slot {
-  cudaStream_t stream = nullptr;
-  void* pin_in = nullptr;  // chunk staging (stamps + offsets)
-  size_t pin_in_bytes = 0;
-  void* d_chunk = nullptr;  // device copy of the chunk
-  size_t d_chunk_bytes = 0;
+  cudaStream_t stream = nullptr;       // sketches, reconstruction, result copies
+  cudaStream_t copy_stream = nullptr;  // chunk uploads
+  // two chunk buffers alternate so that the upload of chunk i+1 overlaps the
+  // sketch of chunk i
+  void* pin_in[2] = {nullptr, nullptr};  // staging for pageable caller memory
+  size_t pin_in_bytes[2] = {0, 0};
+  void* d_chunk[2] = {nullptr, nullptr};
+  size_t d_chunk_bytes[2] = {0, 0};
+  cudaEvent_t copied[2] = {nullptr, nullptr};    // upload into d_chunk[b] done
+  cudaEvent_t consumed[2] = {nullptr, nullptr};  // sketch reading d_chunk[b] done
+  int next = 0;
+  void* pin_h = nullptr;  // impulse response staging
+  size_t pin_h_bytes = 0;
   void* pin_out = nullptr;  // results
   size_t pin_out_bytes = 0;
-  cudaEvent_t in_done = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
 };
@@ -112,9 +119,22 @@ Serving* serving(srt3d_ctx* ctx) {
 
 srt3d_status ensure_slot(srt3d_ctx* ctx, Slot& s) {
   if (!s.stream) SRT3D_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
-  if (!s.in_done) SRT3D_CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming));
+  if (!s.copy_stream) SRT3D_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&s.copy_stream, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b) {
+    if (!s.copied[b]) SRT3D_CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.copied[b], cudaEventDisableTiming));
+    if (!s.consumed[b]) SRT3D_CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.consumed[b], cudaEventDisableTiming));
+  }
   if (!s.done) SRT3D_CUDA_TRY(ctx, cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
   return SRT3D_OK;
+}
+
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 srt3d_status grow_pinned(srt3d_ctx* ctx, void** p, size_t* have, size_t want) {
@@ -150,11 +170,17 @@ void serving_destroy(srt3d_ctx* ctx) {
   }
   for (Slot& s : sv->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.d_chunk) cudaFree(s.d_chunk);
-    if (s.pin_in) cudaFreeHost(s.pin_in);
+    if (s.copy_stream) cudaStreamSynchronize(s.copy_stream);
+    for (int b = 0; b < 2; ++b) {
+      if (s.d_chunk[b]) cudaFree(s.d_chunk[b]);
+      if (s.pin_in[b]) cudaFreeHost(s.pin_in[b]);
+      if (s.copied[b]) cudaEventDestroy(s.copied[b]);
+      if (s.consumed[b]) cudaEventDestroy(s.consumed[b]);
+    }
+    if (s.pin_h) cudaFreeHost(s.pin_h);
     if (s.pin_out) cudaFreeHost(s.pin_out);
-    if (s.in_done) cudaEventDestroy(s.in_done);
     if (s.done) cudaEventDestroy(s.done);
+    if (s.copy_stream) cudaStreamDestroy(s.copy_stream);
     if (s.stream) cudaStreamDestroy(s.stream);
   }
   delete sv;
@@ -221,13 +247,12 @@ extern "C" srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t
     SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(f->S, 0, size_t(P) * m * sizeof(float2), s.stream));
     SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(f->n, 0, size_t(P) * sizeof(uint32_t), s.stream));
     SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(f->flags, 0, sizeof(uint32_t), s.stream));
-    // h travels through the staging buffer like a chunk
-    SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.in_done));
-    st = grow_pinned(ctx, &s.pin_in, &s.pin_in_bytes, size_t(T) * sizeof(float));
+    // h: the previous frame of this slot finished (it was polled), so its
+    // staging buffer is free
+    st = grow_pinned(ctx, &s.pin_h, &s.pin_h_bytes, size_t(T) * sizeof(float));
     if (st != SRT3D_OK) return st;
-    std::memcpy(s.pin_in, h, size_t(T) * sizeof(float));
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(f->h, s.pin_in, size_t(T) * sizeof(float), cudaMemcpyHostToDevice, s.stream));
-    SRT3D_CUDA_TRY(ctx, cudaEventRecord(s.in_done, s.stream));
+    std::memcpy(s.pin_h, h, size_t(T) * sizeof(float));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(f->h, s.pin_h, size_t(T) * sizeof(float), cudaMemcpyHostToDevice, s.stream));
   } else {
     f = it->second;
     if (f->closed) return set_error(ctx, SRT3D_EINVAL, "frame already received its last chunk");
@@ -235,29 +260,45 @@ extern "C" srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t
       return set_error(ctx, SRT3D_EINVAL, "chunk shape differs from the frame's first chunk");
   }
   Slot& s = sv->slots[f->slot];
-  // stage the chunk: the previous copy out of the staging buffer must be done
+  // upload the chunk into the buffer not used by the previous chunk; pinned
+  // caller memory is copied directly, pageable memory through staging
+  const int b = s.next;
+  s.next ^= 1;
   const size_t sb = al256(N * sizeof(uint16_t)), ob = size_t(P + 1) * sizeof(uint32_t);
-  SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.in_done));
-  st = grow_pinned(ctx, &s.pin_in, &s.pin_in_bytes, sb + ob);
-  if (st != SRT3D_OK) return st;
-  if (s.d_chunk_bytes < sb + ob) {
-    SRT3D_CUDA_TRY(ctx, cudaStreamSynchronize(s.stream));
-    if (s.d_chunk) SRT3D_CUDA_TRY(ctx, cudaFree(s.d_chunk));
-    s.d_chunk = nullptr;
-    s.d_chunk_bytes = 0;
+  if (s.d_chunk_bytes[b] < sb + ob) {
+    SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.consumed[b]));
+    if (s.d_chunk[b]) SRT3D_CUDA_TRY(ctx, cudaFree(s.d_chunk[b]));
+    s.d_chunk[b] = nullptr;
+    s.d_chunk_bytes[b] = 0;
     const size_t want = al256((sb + ob) + (sb + ob) / 4);
-    SRT3D_CUDA_TRY(ctx, cudaMalloc(&s.d_chunk, want));
-    s.d_chunk_bytes = want;
+    SRT3D_CUDA_TRY(ctx, cudaMalloc(&s.d_chunk[b], want));
+    s.d_chunk_bytes[b] = want;
   }
-  char* pin = static_cast<char*>(s.pin_in);
-  if (N) std::memcpy(pin, chunk_stamps, N * sizeof(uint16_t));
-  std::memcpy(pin + sb, chunk_offsets, ob);
-  SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(s.d_chunk, pin, sb + ob, cudaMemcpyHostToDevice, s.stream));
-  SRT3D_CUDA_TRY(ctx, cudaEventRecord(s.in_done, s.stream));
-  const uint16_t* d_st = static_cast<const uint16_t*>(s.d_chunk);
-  const uint32_t* d_off = reinterpret_cast<const uint32_t*>(static_cast<char*>(s.d_chunk) + sb);
+  char* dc = static_cast<char*>(s.d_chunk[b]);
+  SRT3D_CUDA_TRY(ctx, cudaStreamWaitEvent(s.copy_stream, s.consumed[b], 0));
+  const bool direct = N && is_pinned(chunk_stamps) && is_pinned(chunk_offsets);
+  if (direct) {
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(dc, chunk_stamps, N * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                                        s.copy_stream));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(dc + sb, chunk_offsets, ob, cudaMemcpyHostToDevice, s.copy_stream));
+  } else {
+    SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.copied[b]));  // staging buffer b free again
+    st = grow_pinned(ctx, &s.pin_in[b], &s.pin_in_bytes[b], sb + ob);
+    if (st != SRT3D_OK) return st;
+    char* pin = static_cast<char*>(s.pin_in[b]);
+    if (N) std::memcpy(pin, chunk_stamps, N * sizeof(uint16_t));
+    std::memcpy(pin + sb, chunk_offsets, ob);
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(dc, pin, sb + ob, cudaMemcpyHostToDevice, s.copy_stream));
+  }
+  SRT3D_CUDA_TRY(ctx, cudaEventRecord(s.copied[b], s.copy_stream));
+  SRT3D_CUDA_TRY(ctx, cudaStreamWaitEvent(s.stream, s.copied[b], 0));
+  const uint16_t* d_st = reinterpret_cast<const uint16_t*>(dc);
+  const uint32_t* d_off = reinterpret_cast<const uint32_t*>(dc + sb);
   st = launch_sketch_stream(ctx, d_st, d_off, N, P, T, m, 1, f->S, f->n, s.stream, f->flags);
   if (st != SRT3D_OK) return st;
+  SRT3D_CUDA_TRY(ctx, cudaEventRecord(s.consumed[b], s.stream));
+  // the caller's arrays must be free to reuse when submit returns
+  if (direct) SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.copied[b]));
   if (last_chunk) {
     f->closed = true;
     st = launch_finalize(ctx, f->S, f->n, P, m, f->S, s.stream);
