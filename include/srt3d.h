@@ -179,6 +179,37 @@ srt3d_status srt3d_reconstruct(srt3d_ctx* ctx, const float* z, const uint32_t* n
                                const srt3d_params* params, float* depth, float* alpha,
                                uint8_t* active, float* alpha0, void* stream);
 
+/* One frame of a batch (srt3d_process_batch). All pointers are device
+ * pointers owned by the caller; P = rows * cols. */
+typedef struct srt3d_frame {
+  const uint16_t* stamps;  /* uint16 [num_stamps], pixel-sorted (Sec. 2, Eq. 1)        */
+  const uint32_t* offsets; /* uint32 [P + 1], CSR offsets                               */
+  uint64_t num_stamps;
+  uint32_t rows, cols;     /* N_r x N_c (Sec. 3)                                        */
+  uint32_t T, m;           /* time bins, sketch size (Sec. 2, Eq. 3)                    */
+  const float* h;          /* float [T], impulse response by circular lag              */
+  float* z;                /* float [P][m][2]: out, normalised sketch (Eq. 3)           */
+  uint32_t* n;             /* uint32 [P]: out, photon counts                            */
+  float* depth;            /* float [P][k_max]: out                                     */
+  float* alpha;            /* float [P][k_max]: out                                     */
+  uint8_t* active;         /* uint8 [P][k_max]: out                                     */
+  float* alpha0;           /* float [P]: out                                            */
+} srt3d_frame;
+
+/* Sketch, normalise and reconstruct a batch of frames of different sizes, T,
+ * m and photon densities (Sec. 2, Eq. 3; Sec. 3, Eq. 8), each stage as one
+ * launch over all frames, the whole batch as one CUDA graph. The first call
+ * for a given set of frames (pointers and shapes) and params tunes the
+ * sketch's lanes per pixel for any new photon-density class (a few timed
+ * launches that write z and n), builds the work lists and captures the graph
+ * (synchronising); later calls with the same frames only launch the graph on
+ * `stream`. params->init_mode must be SRT3D_INIT_MATCHED and
+ * params->regularize 1. Results equal those of srt3d_sketch_stream +
+ * srt3d_finalize + srt3d_reconstruct per frame up to the FP32 summation
+ * order of the sketch. */
+srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* frames, uint32_t num_frames,
+                                 const srt3d_params* params, void* stream);
+
 /* Allocation-free variant of srt3d_reconstruct (the paper has no
  * counterpart; same arguments and results). For callers that cannot allocate
  * device memory while they reconstruct: a real-time lidar loop in which

@@ -56,6 +56,25 @@ def make_params(iters=20, k_max=1, radius=1, init_mode=SRT3D_INIT_MATCHED, regul
                         smooth_lambda, min_sep)
 
 
+class srt3d_frame(ctypes.Structure):
+    _fields_ = [
+        ("stamps", ctypes.c_void_p),
+        ("offsets", ctypes.c_void_p),
+        ("num_stamps", ctypes.c_uint64),
+        ("rows", ctypes.c_uint32),
+        ("cols", ctypes.c_uint32),
+        ("T", ctypes.c_uint32),
+        ("m", ctypes.c_uint32),
+        ("h", ctypes.c_void_p),
+        ("z", ctypes.c_void_p),
+        ("n", ctypes.c_void_p),
+        ("depth", ctypes.c_void_p),
+        ("alpha", ctypes.c_void_p),
+        ("active", ctypes.c_void_p),
+        ("alpha0", ctypes.c_void_p),
+    ]
+
+
 class SRT3DError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} ({status})")
@@ -224,6 +243,7 @@ _SIGS.update({
     "srt3d_profile_read": (_i32, [_vp, _u32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "srt3d_kernel_count": (_u32, []),
     "srt3d_kernel_name": (ctypes.c_char_p, [_u32]),
+    "srt3d_process_batch": (_i32, [_vp, ctypes.POINTER(srt3d_frame), _u32, ctypes.POINTER(srt3d_params), _vp]),
     "srt3d_reconstruct_noalloc": (_i32, [_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, ctypes.POINTER(srt3d_params),
                                          _vp, _vp, _vp, _vp, _vp]),
 })
@@ -269,3 +289,20 @@ def profile_totals(ctx):
         if cnt:
             out[srt3d_kernel_name(k)] = (ms, cnt)
     return out
+
+
+def make_frame(stamps, offsets, rows, cols, T, m, h, z, n, depth, alpha, active, alpha0):
+    """srt3d_frame from torch CUDA tensors (device pointers)."""
+    import torch
+
+    return srt3d_frame(_dev(stamps, torch.int16, "stamps").value if stamps.numel() else None,
+                       _dev(offsets, torch.int32, "offsets"), stamps.numel(), int(rows), int(cols), int(T), int(m),
+                       _dev(h, torch.float32, "h"), _dev(z, torch.float32, "z"), _dev(n, torch.int32, "n"),
+                       _dev(depth, torch.float32, "depth"), _dev(alpha, torch.float32, "alpha"),
+                       _dev(active, torch.uint8, "active"), _dev(alpha0, torch.float32, "alpha0"))
+
+
+def srt3d_process_batch(ctx, frames, params, stream=None):
+    arr = (srt3d_frame * len(frames))(*frames)
+    st = lib().srt3d_process_batch(ctx, arr, len(frames), ctypes.byref(params), _stream(stream))
+    return _check(ctx, st, "srt3d_process_batch")

@@ -149,6 +149,7 @@ void srt3d_destroy(srt3d_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   serving_destroy(ctx);
+  batch_destroy(ctx);
   cudaDeviceSynchronize();
   for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
   for (auto& kv : ctx->fourier) cudaFree(kv.second.ptr);

@@ -41,6 +41,30 @@ struct DevBuf {
 
 struct Serving;  // serving runtime (serve.cu)
 
+// One frame of a batch (srt3d_process_batch), as the batched kernels see it.
+struct BatchFrame {
+  const uint16_t* stamps;
+  const uint32_t* offsets;
+  uint32_t num_stamps;
+  uint32_t rows, cols, P, T, m;
+  int glog2;  // sketch lanes per pixel (log2), from the autotuner
+  const float2* table;
+  uint32_t tab_entries;
+  int two_level;
+  const float* h;
+  float2* S;  // sketch state, then z in place
+  uint32_t* n;
+  float* depth;
+  float* alpha;
+  uint8_t* active;
+  float* alpha0;
+  float2* hh;  // per-frame reconstruction scratch: hhat [32], misc [8]
+  float* misc;
+  uint32_t D;        // matched-filter grid spacing
+  uint32_t tile0;    // first iteration tile of this frame in the batch
+  uint32_t tiles_x;  // iteration tiles per row
+};
+
 // Kernel ids for the profiling counters.
 enum KernelId : uint32_t {
   KID_SKETCH_STREAM = 0,
@@ -53,6 +77,7 @@ enum KernelId : uint32_t {
   KID_GRAD,
   KID_ITER,
   KID_ALPHA0,
+  KID_BATCH,
   KID_COUNT
 };
 
@@ -105,6 +130,20 @@ srt3d_status launch_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const 
                                   uint32_t* flags = nullptr);
 srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n, uint32_t P,
                              uint32_t m, float2* z, cudaStream_t stream);
+int sketch_round_m(uint32_t m);
+int sketch_default_glog2(double mean_photons_per_pixel);
+srt3d_status launch_sketch_stream_g(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                    uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int accumulate,
+                                    float2* S, uint32_t* n, cudaStream_t stream, uint32_t* flags, int glog2);
+srt3d_status launch_sketch_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const uint3* d_items,
+                                 uint32_t num_items, int M, uint32_t max_tab_entries, cudaStream_t stream);
+srt3d_status launch_finalize_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
+                                   uint32_t max_pm, cudaStream_t stream);
+srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
+                                      const uint3* d_init_items, uint32_t num_init_items, uint32_t total_tiles,
+                                      uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
+                                      cudaStream_t stream);
+uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m);
 srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                      uint64_t num_stamps, uint32_t P, uint32_t T, uint16_t* hist,
                                      cudaStream_t stream);
@@ -117,6 +156,7 @@ srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint3
                              const srt3d_params* prm);
 
 void serving_destroy(srt3d_ctx* ctx);
+void batch_destroy(srt3d_ctx* ctx);
 
 // Profiling: prof_begin returns an event pair (or {nullptr,nullptr} when off)
 // recorded around one launch on `stream`.

@@ -72,11 +72,10 @@ __device__ __forceinline__ void load_table(float2* s_tab, const float2* table, u
 
 // One block: hhat (FP32 partial sums per thread, then a tree), H, n_max, and
 // the step-size bases eta_t * n_max, eta_alpha * n_max.
-__global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
-                                               uint32_t P, uint32_t T, uint32_t m, uint32_t K,
-                                               const float2* __restrict__ table, uint32_t entries, int two_level,
-                                               float2* __restrict__ hh_out, float* __restrict__ misc) {
-  extern __shared__ float2 s_tab[];
+__device__ __forceinline__ void prep_body(const float* __restrict__ h, const uint32_t* __restrict__ n, uint32_t P,
+                                          uint32_t T, uint32_t m, uint32_t K, const float2* __restrict__ table,
+                                          uint32_t entries, int two_level, float2* __restrict__ hh_out,
+                                          float* __restrict__ misc, float2* s_tab) {
   __shared__ float s_red[2][32];
   __shared__ float s_H;
   __shared__ uint32_t s_nmax;
@@ -146,6 +145,21 @@ __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, cons
   }
 }
 
+__global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
+                                               uint32_t P, uint32_t T, uint32_t m, uint32_t K,
+                                               const float2* __restrict__ table, uint32_t entries, int two_level,
+                                               float2* __restrict__ hh_out, float* __restrict__ misc) {
+  extern __shared__ float2 s_tab[];
+  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, s_tab);
+}
+
+// Batched: one block per frame of the batch.
+__global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restrict__ frames, uint32_t K) {
+  extern __shared__ float2 s_tab[];
+  const BatchFrame& f = frames[blockIdx.x];
+  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc, s_tab);
+}
+
 // Matched-filter score s(t) = Re sum_{l=1}^{m} c_l w^l for w = e^{-i 2 pi t / T},
 // by complex Horner (4 FFMA per harmonic). `we` is e^{+i 2 pi t / T}.
 __device__ __forceinline__ float mf_score(const float2* c, uint32_t m, float2 we) {
@@ -177,7 +191,7 @@ __device__ __forceinline__ void mf_take(float s, uint32_t t, float& bs, uint32_t
 // D <= 64 with w_m^2 D^2 / 8 <= 0.02, so that for every pixel the curvature
 // term M2 D^2 / 8 stays below 2% of M0 (M2 <= w_m^2 M0). G = ceil(T / D) is
 // then at most 1024.
-uint32_t mf_grid_spacing(uint32_t T, uint32_t m) {
+uint32_t mf_grid_spacing_impl(uint32_t T, uint32_t m) {
   const double w = 2.0 * M_PI * double(m) / double(T);
   uint32_t D = 64u;
   while (D > 1u && w * w * double(D) * double(D) / 8.0 > 0.02) D >>= 1;
@@ -272,6 +286,83 @@ __device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, 
   *best_t = bt;
 }
 
+// Matched-filter initialisation of pixel p by one warp (see warp_argmax_scores).
+template <int K>
+__device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict__ z, const uint32_t* __restrict__ n,
+                                           uint32_t T, uint32_t m, const float2* s_tab, bool tl,
+                                           const float2* s_wg, float* s_grid, uint32_t D, uint32_t G,
+                                           const float2* s_hh, float E2, float prune_alpha, float min_sep,
+                                           float2* c, float* __restrict__ depth, float* __restrict__ alpha,
+                                           uint8_t* __restrict__ active, float* __restrict__ alpha0) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const float invT = 1.0f / float(T);
+  const uint32_t cnt = n[p];
+  if (lane < m) {
+    const float2 zl = z[size_t(p) * m + lane];
+    const float2 hc = make_float2(s_hh[lane].x, -s_hh[lane].y);
+    c[lane] = cmul(hc, zl);
+  }
+  __syncwarp();
+  float s1;
+  uint32_t t1;
+  warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, -1, 0.f, &s1, &t1);
+  if (t1 >= T) {  // no finite score (cannot happen for finite z)
+    t1 = 0u;
+    s1 = 0.f;
+  }
+  float a[K], t[K];
+  bool act[K];
+  a[0] = fmaxf(0.f, s1 / E2);
+  t[0] = float(t1);
+  act[0] = (a[0] >= prune_alpha) && cnt > 0;
+  if (K == 2) {
+    __syncwarp();
+    if (lane < m) {
+      const float2 zl = z[size_t(p) * m + lane];
+      const float2 hv = s_hh[lane];
+      const float2 e = phase(s_tab, mulmod(lane + 1u, t1, T, invT), tl);
+      const float f = (a[0] >= prune_alpha) ? a[0] : 0.f;
+      const float2 fit = cmul(hv, e);
+      const float2 r = make_float2(zl.x - f * fit.x, zl.y - f * fit.y);
+      c[lane] = cmul(make_float2(hv.x, -hv.y), r);
+    }
+    __syncwarp();
+    float s2;
+    uint32_t t2;
+    warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, int(t1), min_sep, &s2, &t2);
+    if (t2 >= T) {
+      t2 = 0u;
+      s2 = 0.f;
+    }
+    a[K - 1] = fmaxf(0.f, s2 / E2);
+    t[K - 1] = float(t2);
+    act[K - 1] = (a[K - 1] >= prune_alpha) && cnt > 0;
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (!act[k]) a[k] = 0.f;
+    sum += a[k];
+  }
+  if (sum > 1.f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
+    sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sum += a[k];
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      depth[size_t(p) * K + k] = t[k];
+      alpha[size_t(p) * K + k] = a[k];
+      active[size_t(p) * K + k] = act[k] ? 1 : 0;
+    }
+    alpha0[p] = 1.f - sum;
+  }
+  __syncwarp();
+}
+
 // Matched-filter initialisation, one warp per pixel. Dynamic shared memory:
 // the phase table, the coarse table e^{i 2 pi g D / T} (G entries) and one
 // row of G grid scores per warp.
@@ -295,78 +386,48 @@ __global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, c
   __syncthreads();
   for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * D, tl);
   __syncthreads();
-  const float invT = 1.0f / float(T);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t warp = threadIdx.x >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   const float E2 = misc[MISC_E2];
-  float2* c = s_c[warp];
-  float* s_grid = s_grid_all + warp * G;
-  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb) {
-    const uint32_t cnt = n[p];
-    if (lane < m) {
-      const float2 zl = z[size_t(p) * m + lane];
-      const float2 hc = make_float2(s_hh[lane].x, -s_hh[lane].y);
-      c[lane] = cmul(hc, zl);
+  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb)
+    init_pixel<K>(p, z, n, T, m, s_tab, tl, s_wg, s_grid_all + warp * G, D, G, s_hh, E2, prune_alpha, min_sep,
+                  s_c[warp], depth, alpha, active, alpha0);
+}
+
+// Batched initialisation: items (frame, first pixel, last pixel); the CTA
+// reloads the tables when the frame changes. Dynamic shared memory is sized
+// for the largest frame of the batch.
+template <int K>
+__global__ void __launch_bounds__(kBlock) k_init_batch(const BatchFrame* __restrict__ frames,
+                                                       const uint3* __restrict__ items, uint32_t num_items,
+                                                       uint32_t max_entries, uint32_t max_G, float prune_alpha,
+                                                       float min_sep) {
+  extern __shared__ float2 s_tab[];
+  __shared__ float2 s_c[kBlock / 32][kMaxM];
+  __shared__ float2 s_hh[kMaxM];
+  float2* s_wg = s_tab + max_entries;
+  float* s_grid_all = reinterpret_cast<float*>(s_wg + max_G);
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t wpb = blockDim.x >> 5;
+  uint32_t cur = 0xffffffffu;
+  for (uint32_t it = blockIdx.x; it < num_items; it += gridDim.x) {
+    const uint3 item = items[it];
+    const BatchFrame& f = frames[item.x];
+    const uint32_t G = (f.T + f.D - 1u) / f.D;
+    const bool tl = f.two_level != 0;
+    if (item.x != cur) {
+      __syncthreads();
+      if (threadIdx.x < f.m) s_hh[threadIdx.x] = f.hh[threadIdx.x];
+      for (uint32_t i = threadIdx.x; i < f.tab_entries; i += blockDim.x) s_tab[i] = f.table[i];
+      __syncthreads();
+      for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * f.D, tl);
+      __syncthreads();
+      cur = item.x;
     }
-    __syncwarp();
-    float s1;
-    uint32_t t1;
-    warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, -1, 0.f, &s1, &t1);
-    if (t1 >= T) {  // no finite score (cannot happen for finite z)
-      t1 = 0u;
-      s1 = 0.f;
-    }
-    float a[K], t[K];
-    bool act[K];
-    a[0] = fmaxf(0.f, s1 / E2);
-    t[0] = float(t1);
-    act[0] = (a[0] >= prune_alpha) && cnt > 0;
-    if (K == 2) {
-      __syncwarp();
-      if (lane < m) {
-        const float2 zl = z[size_t(p) * m + lane];
-        const float2 hv = s_hh[lane];
-        const float2 e = phase(s_tab, mulmod(lane + 1u, t1, T, invT), tl);
-        const float f = (a[0] >= prune_alpha) ? a[0] : 0.f;
-        const float2 fit = cmul(hv, e);
-        const float2 r = make_float2(zl.x - f * fit.x, zl.y - f * fit.y);
-        c[lane] = cmul(make_float2(hv.x, -hv.y), r);
-      }
-      __syncwarp();
-      float s2;
-      uint32_t t2;
-      warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, int(t1), min_sep, &s2, &t2);
-      if (t2 >= T) {
-        t2 = 0u;
-        s2 = 0.f;
-      }
-      a[K - 1] = fmaxf(0.f, s2 / E2);
-      t[K - 1] = float(t2);
-      act[K - 1] = (a[K - 1] >= prune_alpha) && cnt > 0;
-    }
-    float sum = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (!act[k]) a[k] = 0.f;
-      sum += a[k];
-    }
-    if (sum > 1.f) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
-      sum = 0.f;
-#pragma unroll
-      for (int k = 0; k < K; ++k) sum += a[k];
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        depth[size_t(p) * K + k] = t[k];
-        alpha[size_t(p) * K + k] = a[k];
-        active[size_t(p) * K + k] = act[k] ? 1 : 0;
-      }
-      alpha0[p] = 1.f - sum;
-    }
-    __syncwarp();
+    const float E2 = f.misc[MISC_E2];
+    for (uint32_t p = item.y + warp; p < item.z; p += wpb)
+      init_pixel<K>(p, f.S, f.n, f.T, f.m, s_tab, tl, s_wg, s_grid_all + warp * max_G, f.D, G, s_hh, E2, prune_alpha,
+                    min_sep, s_c[warp], f.depth, f.alpha, f.active, f.alpha0);
   }
 }
 
@@ -537,10 +598,11 @@ __host__ __device__ constexpr int iter_threads() {
 }
 
 template <int K, int R>
-__global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const float2* __restrict__ z,
-                                                   const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
-                                                   const float2* __restrict__ hh_g, const float* __restrict__ misc,
-                                                   float* depth, float* alpha, uint8_t* active, float* alpha0) {
+__device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uint32_t tile_y,
+                                          const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
+                                          uint32_t m, const float2* __restrict__ hh_g,
+                                          const float* __restrict__ misc, float* depth, float* alpha,
+                                          uint8_t* active, float* alpha0) {
   constexpr int H = 2 * R;
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
   constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
@@ -552,7 +614,7 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const fl
   const int tid = threadIdx.x;
   if (tid < int(m)) s_hh[tid] = hh_g[tid];
   __syncthreads();
-  const int r0 = int(blockIdx.y) * kTH, c0 = int(blockIdx.x) * kTW;
+  const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
   const float nmax = misc[MISC_NMAX];
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   // 1) gradient step on the region (pixels outside the array are inactive)
@@ -697,6 +759,38 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const fl
   alpha0[p] = 1.f - sum;
 }
 
+template <int K, int R>
+__global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const float2* __restrict__ z,
+                                                            const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
+                                                            const float2* __restrict__ hh_g,
+                                                            const float* __restrict__ misc, float* depth,
+                                                            float* alpha, uint8_t* active, float* alpha0) {
+  iter_tile<K, R>(st, blockIdx.x, blockIdx.y, z, n, T, m, hh_g, misc, depth, alpha, active, alpha0);
+}
+
+// Batched iteration: one CTA per tile of every frame of the batch (frames
+// located by a binary search over their first tile index).
+template <int K, int R>
+__global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
+                                                                  const BatchFrame* __restrict__ frames,
+                                                                  uint32_t nframes) {
+  uint32_t lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) / 2;
+    if (frames[mid].tile0 <= blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const BatchFrame& f = frames[lo];
+  const uint32_t t = blockIdx.x - f.tile0;
+  Stencil st = base;
+  st.rows = f.rows;
+  st.cols = f.cols;
+  iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth, f.alpha, f.active,
+                  f.alpha0);
+}
+
 template <int K>
 __global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint8_t* __restrict__ active,
                          float* __restrict__ alpha0) {
@@ -724,7 +818,7 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   if (prm.init_mode == SRT3D_INIT_MATCHED) {
-    const uint32_t D = mf_grid_spacing(T, m);
+    const uint32_t D = mf_grid_spacing_impl(T, m);
     const uint32_t G = (T + D - 1u) / D;
     const size_t init_smem = tab_smem + size_t(G) * sizeof(float2) + size_t(kBlock / 32) * G * sizeof(float);
     if (init_smem > 48 * 1024)
@@ -780,7 +874,73 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   return SRT3D_OK;
 }
 
+template <int K>
+srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const uint3* d_items,
+                       uint32_t num_items, uint32_t total_tiles, uint32_t max_entries, uint32_t max_G,
+                       const srt3d_params& prm, cudaStream_t stream) {
+  const size_t tab_smem = size_t(max_entries) * sizeof(float2);
+  if (tab_smem > 48 * 1024)
+    SRT3D_CUDA_TRY(ctx,
+                   cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+  {
+    const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
+    k_prep_batch<<<nframes, 1024, tab_smem, stream>>>(d_frames, K);
+    prof_end(ctx, KID_PREP, mk, stream);
+  }
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  const size_t init_smem = tab_smem + size_t(max_G) * sizeof(float2) + size_t(kBlock / 32) * max_G * sizeof(float);
+  if (init_smem > 48 * 1024)
+    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(init_smem)));
+  int bps = 0;
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init_batch<K>, kBlock, init_smem));
+  if (bps < 1) bps = 1;
+  const uint32_t grid = std::min<uint32_t>(num_items, uint32_t(ctx->num_sms) * uint32_t(bps));
+  {
+    const ProfMark mk = prof_begin(ctx, KID_INIT, stream);
+    k_init_batch<K><<<grid, kBlock, init_smem, stream>>>(d_frames, d_items, num_items, max_entries, max_G,
+                                                        prm.prune_alpha, prm.min_sep);
+    prof_end(ctx, KID_INIT, mk, stream);
+  }
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  Stencil st;
+  st.rows = 0;
+  st.cols = 0;
+  st.radius = prm.radius;
+  st.h2 = prm.apss_h * prm.apss_h;
+  st.inv_h2 = 1.f / st.h2;
+  st.d_max = prm.d_max;
+  st.ds = prm.depth_scale;
+  st.lambda = prm.smooth_lambda;
+  st.prune_alpha = prm.prune_alpha;
+  for (uint32_t it = 0; it < prm.iters; ++it) {
+    const ProfMark mk = prof_begin(ctx, KID_ITER, stream);
+    if (prm.radius == 1)
+      k_iter_batch<K, 1><<<total_tiles, iter_threads<1>(), 0, stream>>>(st, d_frames, nframes);
+    else if (prm.radius == 2)
+      k_iter_batch<K, 2><<<total_tiles, iter_threads<2>(), 0, stream>>>(st, d_frames, nframes);
+    else
+      k_iter_batch<K, 3><<<total_tiles, iter_threads<3>(), 0, stream>>>(st, d_frames, nframes);
+    prof_end(ctx, KID_ITER, mk, stream);
+    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return SRT3D_OK;
+}
+
 }  // namespace
+
+uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m) { return mf_grid_spacing_impl(T, m); }
+
+srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
+                                      const uint3* d_init_items, uint32_t num_init_items, uint32_t total_tiles,
+                                      uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
+                                      cudaStream_t stream) {
+  if (prm.k_max == 1)
+    return run_batch<1>(ctx, d_frames, nframes, d_init_items, num_init_items, total_tiles, max_tab_entries, max_G,
+                        prm, stream);
+  return run_batch<2>(ctx, d_frames, nframes, d_init_items, num_init_items, total_tiles, max_tab_entries, max_G,
+                      prm, stream);
+}
 
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
   (void)m;

@@ -47,6 +47,12 @@ def test_params_struct_layout_matches_header():
     assert binding.srt3d_params.min_sep.offset == 40
 
 
+def test_frame_struct_layout_matches_header():
+    # 3 x 8-byte fields, 4 x uint32, 7 pointers
+    assert ctypes.sizeof(binding.srt3d_frame) == 96
+    assert binding.srt3d_frame.h.offset == 40
+
+
 def test_status_strings(lib):
     assert binding.lib().srt3d_status_string(binding.SRT3D_ERANGE) == b"SRT3D_ERANGE"
     assert binding.lib().srt3d_status_string(12345) == b"SRT3D_UNKNOWN"
