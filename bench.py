@@ -46,8 +46,9 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
-    ap.add_argument("--only", choices=["all", "step", "hist", "serving"], default="all")
+    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch"], default="all")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -385,6 +386,57 @@ def serving_section(B, dev, seconds):
                     "host memory"}
 
 
+# ----------------------------------------------------------------- batched uneven frames
+
+def batch_section(B, ctx, dev, steps, flush):
+    """64 uneven frames (sizes {64,128,256,512}^2, T in {1024,4096}, m in
+    {4,16}, photons/px log-uniform [10,5000], SBR log-uniform [0.05,5]) through
+    srt3d_process_batch: one launch per stage over all frames, one CUDA graph
+    per batch. The first call tunes and captures; the timed calls replay."""
+    import numpy as np
+    import torch
+
+    from paper_2203_00952_gb300 import synth
+
+    specs = synth.batch_specs(64)
+    frames, keep = [], []
+    photons = 0
+    for i, (spec, m) in enumerate(specs):
+        st, off, _ = synth.make_stream_frame_torch(spec, synth.SEED_BATCH, i, device=dev)
+        P = spec.num_pixels
+        h = torch.from_numpy(synth.impulse_response(spec.T, spec.sigma).astype(np.float32)).to(dev)
+        bufs = (torch.empty(P, m, 2, device=dev), torch.empty(P, dtype=torch.int32, device=dev),
+                torch.empty(P, 2, device=dev), torch.empty(P, 2, device=dev),
+                torch.empty(P, 2, dtype=torch.uint8, device=dev), torch.empty(P, device=dev))
+        frames.append(B.make_frame(st, off, spec.rows, spec.cols, spec.T, m, h, *bufs))
+        keep.append((st, off, h, bufs))
+        photons += st.numel()
+    prm = B.make_params(iters=20, k_max=2, d_max=36.0, min_sep=18.0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    B.srt3d_process_batch(ctx, frames, prm, stream)
+    B.srt3d_sync(ctx, stream)
+    setup_s = time.perf_counter() - t0
+    for _ in range(2):
+        B.srt3d_process_batch(ctx, frames, prm, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        B.srt3d_process_batch(ctx, frames, prm, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    B.srt3d_sync(ctx, stream)
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    del keep, frames
+    torch.cuda.empty_cache()
+    return {"workload": "batch64_uneven_T1024-4096_m4-16_K2_it20", "frames": len(specs), "photons": photons,
+            "ms_per_batch": ms, "photons_per_s": photons / (ms / 1e3), "frames_per_s": len(specs) / (ms / 1e3),
+            "first_call_s": setup_s,
+            "launch": "one CUDA graph per batch: one sketch launch per m class, then finalize, prep, init and "
+                      "20 iteration launches, each over all frames"}
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def load_peaks():
@@ -444,6 +496,14 @@ def gpu_arm(args):
         res = serving_section(B, dev, args.serving_seconds)
         if rank == 0:
             print(json.dumps({"serving": res}), flush=True)
+        return
+    if args.only == "batch":
+        ctx = B.srt3d_create(local)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        res = batch_section(B, ctx, dev, args.batch_steps, flush)
+        B.srt3d_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"batch": res}), flush=True)
         return
     if args.only == "hist":
         # histogram path alone (for profiling): no step timing, no baseline
@@ -553,9 +613,13 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
     d2h = sum(o.nbytes for o in outs if o is not None)
 
-    hist = None
+    hist = batch = None
     if args.only in ("all", "hist") and rank == 0:
         hist = hist_section(B, ctx, dev, args.hist_steps, flush)
+    if args.only == "all" and rank == 0:
+        del stamps, offsets, S, z
+        torch.cuda.empty_cache()
+        batch = batch_section(B, ctx, dev, args.batch_steps, flush)
     B.srt3d_destroy(ctx)
     serving = None
     if args.only == "all" and rank == 0 and world == 1:
@@ -627,6 +691,7 @@ def gpu_arm(args):
         "rooflines": rooflines,
         "cpu_baseline": cpu,
         "hist_sketch": hist,
+        "batch": batch,
         "serving": serving,
     }
     print(json.dumps(out), flush=True)

@@ -216,6 +216,50 @@ def make_hist_frame_torch(spec: FrameSpec, seed: int, device="cuda"):
     return hist, truth
 
 
+def make_stream_frame_torch(spec: FrameSpec, seed: int, frame: int = 0, device="cuda", block: int = 65536):
+    """Same recipe as make_stream_frame, drawn with torch on `device` (used for
+    the large benchmark batches; values differ from the numpy draw). Returns
+    (stamps int16 tensor [N] holding the uint16 bit patterns, offsets int32
+    tensor [P+1], truth)."""
+    import torch
+
+    rng = np.random.default_rng(frame_seed(seed, frame))
+    truth = make_truth(spec, rng)
+    S, B = _rates(spec, truth)
+    P, T = spec.num_pixels, spec.T
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 1000003 + int(frame))
+    f64 = dict(dtype=torch.float64, device=device)
+    lam = torch.as_tensor(S * truth.refl.sum(axis=1) + B, **f64)
+    counts = torch.poisson(lam, generator=gen).to(torch.int64)
+    offsets = torch.zeros(P + 1, dtype=torch.int64, device=device)
+    offsets[1:] = torch.cumsum(counts, 0)
+    N = int(offsets[-1].item())
+    if N >= 2**31:
+        raise ValueError("frame exceeds 2^31 photons")
+    stamps = torch.empty(N, dtype=torch.int16, device=device)
+    a1 = torch.as_tensor(truth.alpha[:, 0], **f64)
+    a12 = a1 + torch.as_tensor(truth.alpha[:, 1], **f64)
+    d1 = torch.as_tensor(truth.depth[:, 0], **f64)
+    d2 = torch.as_tensor(np.nan_to_num(truth.depth[:, 1]), **f64)
+    for p0 in range(0, P, block):
+        p1 = min(P, p0 + block)
+        lo, hi = int(offsets[p0].item()), int(offsets[p1].item())
+        if hi == lo:
+            continue
+        pix = torch.repeat_interleave(torch.arange(p0, p1, device=device), counts[p0:p1])
+        u = torch.rand(hi - lo, generator=gen, **f64)
+        g = torch.randn(hi - lo, generator=gen, **f64)
+        bg = torch.randint(0, T, (hi - lo,), generator=gen, device=device)
+        is1 = u < a1[pix]
+        is2 = (~is1) & (u < a12[pix])
+        t = torch.where(is1, d1[pix], d2[pix])
+        sig = torch.remainder(torch.round(t + spec.sigma * g).to(torch.int64), T)
+        val = torch.where(is1 | is2, sig, bg).to(torch.int32)
+        stamps[lo:hi] = torch.where(val >= 32768, val - 65536, val).to(torch.int16)
+    return stamps, offsets.to(torch.int32), truth
+
+
 # Workload shapes (sizes, distributions) used by tests and the benchmark.
 def frame_32x32() -> FrameSpec:
     """32x32 px, T=1024, sigma=4, 100 photons/px, SBR=1, one surface."""
