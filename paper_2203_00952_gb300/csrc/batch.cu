@@ -214,15 +214,25 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   for (auto& kv : sketch_items) items_total += kv.second.size();
   const size_t frames_bytes = al256(num_frames * sizeof(BatchFrame));
   const size_t scratch_per_frame = 512;  // hhat[32] float2 + misc[8] float
-  const size_t bytes = frames_bytes + al256(items_total * sizeof(uint3)) + num_frames * scratch_per_frame;
+  const uint32_t K = params->k_max;
+  size_t alt_bytes = 0;  // alternate state per frame: depth, alpha (float), active (u8)
+  for (uint32_t i = 0; i < num_frames; ++i) alt_bytes += 3 * al256(size_t(hf[i].P) * K * sizeof(float));
+  const size_t bytes =
+      frames_bytes + al256(items_total * sizeof(uint3)) + num_frames * scratch_per_frame + alt_bytes;
   GraphEntry e;
   e.key = key;
   SRT3D_CUDA_TRY(ctx, cudaMalloc(&e.dmem, bytes));
   char* base = static_cast<char*>(e.dmem);
   char* scratch = base + frames_bytes + al256(items_total * sizeof(uint3));
+  char* alt = scratch + num_frames * scratch_per_frame;
   for (uint32_t i = 0; i < num_frames; ++i) {
     hf[i].hh = reinterpret_cast<float2*>(scratch + i * scratch_per_frame);
     hf[i].misc = reinterpret_cast<float*>(scratch + i * scratch_per_frame + 256);
+    const size_t pkb = al256(size_t(hf[i].P) * K * sizeof(float));
+    hf[i].depth_alt = reinterpret_cast<float*>(alt);
+    hf[i].alpha_alt = reinterpret_cast<float*>(alt + pkb);
+    hf[i].active_alt = reinterpret_cast<uint8_t*>(alt + 2 * pkb);
+    alt += 3 * pkb;
   }
   std::vector<uint3> all_items;
   std::vector<std::pair<int, std::pair<size_t, size_t>>> groups;  // M -> (offset, count)

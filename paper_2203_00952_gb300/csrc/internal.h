@@ -60,6 +60,9 @@ struct BatchFrame {
   float* alpha0;
   float2* hh;  // per-frame reconstruction scratch: hhat [32], misc [8]
   float* misc;
+  float* depth_alt;  // alternate state buffers (the iterations ping-pong)
+  float* alpha_alt;
+  uint8_t* active_alt;
   uint32_t D;        // matched-filter grid spacing
   uint32_t tile0;    // first iteration tile of this frame in the batch
   uint32_t tiles_x;  // iteration tiles per row

@@ -601,8 +601,10 @@ template <int K, int R>
 __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uint32_t tile_y,
                                           const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
                                           uint32_t m, const float2* __restrict__ hh_g,
-                                          const float* __restrict__ misc, float* depth, float* alpha,
-                                          uint8_t* active, float* alpha0) {
+                                          const float* __restrict__ misc, const float* __restrict__ depth_in,
+                                          const float* __restrict__ alpha_in, const uint8_t* __restrict__ active_in,
+                                          float* __restrict__ depth, float* __restrict__ alpha,
+                                          uint8_t* __restrict__ active, float* __restrict__ alpha0) {
   constexpr int H = 2 * R;
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
   constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
@@ -627,9 +629,9 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
       const size_t p = size_t(rr) * st.cols + size_t(cc);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        t[k] = depth[p * K + k];
-        a[k] = alpha[p * K + k];
-        act[k] = active[p * K + k] != 0;
+        t[k] = depth_in[p * K + k];
+        a[k] = alpha_in[p * K + k];
+        act[k] = active_in[p * K + k] != 0;
       }
       grad_pixel<K>(z + p * m, n[p], T, m, s_hh, eta_t, eta_a, t, a, act);
     } else {
@@ -759,13 +761,20 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
   alpha0[p] = 1.f - sum;
 }
 
+// The state is read from (depth_in, alpha_in, active_in) and written to
+// (depth, alpha, active): distinct buffers, since neighbouring tiles read
+// each other's state as their halo within the same launch.
 template <int K, int R>
 __global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const float2* __restrict__ z,
                                                             const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
                                                             const float2* __restrict__ hh_g,
-                                                            const float* __restrict__ misc, float* depth,
+                                                            const float* __restrict__ misc,
+                                                            const float* __restrict__ depth_in,
+                                                            const float* __restrict__ alpha_in,
+                                                            const uint8_t* __restrict__ active_in, float* depth,
                                                             float* alpha, uint8_t* active, float* alpha0) {
-  iter_tile<K, R>(st, blockIdx.x, blockIdx.y, z, n, T, m, hh_g, misc, depth, alpha, active, alpha0);
+  iter_tile<K, R>(st, blockIdx.x, blockIdx.y, z, n, T, m, hh_g, misc, depth_in, alpha_in, active_in, depth, alpha,
+                  active, alpha0);
 }
 
 // Batched iteration: one CTA per tile of every frame of the batch (frames
@@ -773,7 +782,7 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const fl
 template <int K, int R>
 __global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
                                                                   const BatchFrame* __restrict__ frames,
-                                                                  uint32_t nframes) {
+                                                                  uint32_t nframes, int from_alt) {
   uint32_t lo = 0, hi = nframes - 1;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) / 2;
@@ -787,8 +796,36 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
   Stencil st = base;
   st.rows = f.rows;
   st.cols = f.cols;
-  iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth, f.alpha, f.active,
-                  f.alpha0);
+  if (from_alt)
+    iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth_alt, f.alpha_alt,
+                    f.active_alt, f.depth, f.alpha, f.active, f.alpha0);
+  else
+    iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth, f.alpha, f.active,
+                    f.depth_alt, f.alpha_alt, f.active_alt, f.alpha0);
+}
+
+// Copy every frame's state to its alternate buffers (one CTA per tile).
+template <int K>
+__global__ void k_copy_state_batch(const BatchFrame* __restrict__ frames, uint32_t nframes) {
+  uint32_t lo = 0, hi = nframes - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) / 2;
+    if (frames[mid].tile0 <= blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const BatchFrame& f = frames[lo];
+  const uint32_t t = blockIdx.x - f.tile0;
+  const uint32_t r = (t / f.tiles_x) * kTH + threadIdx.x / kTW, c = (t % f.tiles_x) * kTW + threadIdx.x % kTW;
+  if (r >= f.rows || c >= f.cols) return;
+  const size_t p = size_t(r) * f.cols + c;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    f.depth_alt[p * K + k] = f.depth[p * K + k];
+    f.alpha_alt[p * K + k] = f.alpha[p * K + k];
+    f.active_alt[p * K + k] = f.active[p * K + k];
+  }
 }
 
 template <int K>
@@ -857,16 +894,35 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   st.lambda = prm.smooth_lambda;
   st.prune_alpha = prm.prune_alpha;
   const dim3 tiles((cols + kTW - 1) / kTW, (rows + kTH - 1) / kTH);
+  // Ping-pong between the caller's state and the scratch copy (t1, a1,
+  // act1): with an odd count the state is first copied to scratch, so that
+  // the last iteration always writes the caller's buffers.
+  const size_t pk = size_t(P) * K;
+  if (prm.regularize && (prm.iters & 1u)) {
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
+  }
   for (uint32_t it = 0; it < prm.iters; ++it) {
     const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);
+    const bool from_scratch = ((prm.iters - it) & 1u) != 0;  // the last iteration reads scratch
+    const float* din = from_scratch ? sc.t1 : depth;
+    const float* ain = from_scratch ? sc.a1 : alpha;
+    const uint8_t* cin = from_scratch ? sc.act1 : active;
+    float* dout = from_scratch ? depth : sc.t1;
+    float* aout = from_scratch ? alpha : sc.a1;
+    uint8_t* cout = from_scratch ? active : sc.act1;
     if (!prm.regularize) {
       k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     } else if (prm.radius == 1) {
-      k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                           aout, cout, alpha0);
     } else if (prm.radius == 2) {
-      k_iter<K, 2><<<tiles, iter_threads<2>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 2><<<tiles, iter_threads<2>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                           aout, cout, alpha0);
     } else {
-      k_iter<K, 3><<<tiles, iter_threads<3>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      k_iter<K, 3><<<tiles, iter_threads<3>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                           aout, cout, alpha0);
     }
     prof_end(ctx, prm.regularize ? KID_ITER : KID_GRAD, mk, stream);
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
@@ -913,14 +969,21 @@ srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nfra
   st.ds = prm.depth_scale;
   st.lambda = prm.smooth_lambda;
   st.prune_alpha = prm.prune_alpha;
+  // ping-pong between each frame's state and its alternate buffers; with an
+  // odd count the state is first copied to the alternates (k_copy_state_batch)
+  if (prm.iters & 1u) {
+    k_copy_state_batch<K><<<total_tiles, kTW * kTH, 0, stream>>>(d_frames, nframes);
+    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  }
   for (uint32_t it = 0; it < prm.iters; ++it) {
+    const int from_alt = ((prm.iters - it) & 1u) ? 1 : 0;
     const ProfMark mk = prof_begin(ctx, KID_ITER, stream);
     if (prm.radius == 1)
-      k_iter_batch<K, 1><<<total_tiles, iter_threads<1>(), 0, stream>>>(st, d_frames, nframes);
+      k_iter_batch<K, 1><<<total_tiles, iter_threads<1>(), 0, stream>>>(st, d_frames, nframes, from_alt);
     else if (prm.radius == 2)
-      k_iter_batch<K, 2><<<total_tiles, iter_threads<2>(), 0, stream>>>(st, d_frames, nframes);
+      k_iter_batch<K, 2><<<total_tiles, iter_threads<2>(), 0, stream>>>(st, d_frames, nframes, from_alt);
     else
-      k_iter_batch<K, 3><<<total_tiles, iter_threads<3>(), 0, stream>>>(st, d_frames, nframes);
+      k_iter_batch<K, 3><<<total_tiles, iter_threads<3>(), 0, stream>>>(st, d_frames, nframes, from_alt);
     prof_end(ctx, KID_ITER, mk, stream);
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   }

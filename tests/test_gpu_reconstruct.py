@@ -76,19 +76,30 @@ def frame_inputs(ctx, spec, seed, m):
     return fr, z, n, to_complex(z), counts(n), h32, hh
 
 
-def compare_state(g, r, n_np, depth_tol, rtol, flip_frac, what):
+def compare_state(g, r, n_np, depth_tol, rtol, flip_frac, what, T=None, outlier_frac=0.0):
+    """Depths are compared on the circle of T bins when T is given (t wraps
+    to [0, T) after a gradient step). `outlier_frac` allows that fraction of
+    the points to exceed the tolerances: points next to a discrete decision
+    that FP32 and FP64 take differently (neighbour gate, weight support,
+    plane-fit acceptance)."""
     tg, ag, actg, a0g = g
     tr, ar, actr, a0r = r
     flips = int(np.count_nonzero(actg != actr))
     npts = actr.size
     assert flips <= max(1, int(flip_frac * npts)), f"{what}: {flips} activity flips of {npts}"
     both = actg & actr
-    dd = np.abs(tg - tr)[both]
-    assert dd.size == 0 or dd.max() <= depth_tol, f"{what}: depth diff {dd.max()}"
+    dd = np.abs(tg - tr)
+    if T is not None:
+        dd = np.minimum(dd, T - dd)
+    dd = dd[both]
     ig = (n_np[:, None] * ag)[both]
     ir = (n_np[:, None] * ar)[both]
     rel = np.abs(ig - ir) / np.maximum(ir, 1e-12)
-    assert rel.size == 0 or rel.max() <= rtol, f"{what}: intensity rel diff {rel.max()}"
+    allowed = int(outlier_frac * npts)
+    bad_d = int(np.count_nonzero(dd > depth_tol))
+    bad_i = int(np.count_nonzero(rel > rtol))
+    assert bad_d <= allowed, f"{what}: {bad_d} depths beyond {depth_tol} (max {dd.max()}), {allowed} allowed"
+    assert bad_i <= allowed, f"{what}: {bad_i} intensities beyond {rtol} (max {rel.max()}), {allowed} allowed"
     return flips
 
 
@@ -154,7 +165,7 @@ def test_one_iteration_from_shared_state(ctx, K, regularize):
     g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=s0[:3], iters=1)
     eta = oracle.step_sizes(hh, n_np.max(), K, spec.T)
     r = oracle.iterate(z_np, n_np, s0[0], s0[1], s0[2], hh, spec.T, spec.rows, spec.cols, p, *eta)
-    compare_state(g, r, n_np, 1e-3, 1e-4, 0.0 if not regularize else FLIP_FRAC, "one iteration")
+    compare_state(g, r, n_np, 1e-3, 1e-4, 0.0 if not regularize else FLIP_FRAC, "one iteration", spec.T)
     same = np.all(g[2] == r[2], axis=1)
     np.testing.assert_allclose(g[3][same], r[3][same], atol=1e-5)
 
@@ -170,7 +181,7 @@ def test_full_reconstruction_from_oracle_init(ctx, K, iters, regularize):
     init = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p)[:3]
     g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=init)
     r = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p, init=init)
-    compare_state(g, r, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, "full reconstruction")
+    compare_state(g, r, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, "full reconstruction", spec.T)
 
 
 def test_full_reconstruction_matched_init_quality(ctx):
@@ -202,7 +213,8 @@ def test_full_reconstruction_matched_init_quality(ctx):
     keep = ~zone.reshape(-1)
     assert keep.mean() > 0.9
     sub = lambda st: tuple(a[keep] for a in st)  # noqa: E731
-    compare_state(sub(g), sub(r), n_np[keep], DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, "matched-init reconstruction")
+    compare_state(sub(g), sub(r), n_np[keep], DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, "matched-init reconstruction",
+                  spec.T)
 
 
 def test_full_size_256x256(ctx):
@@ -221,7 +233,7 @@ def test_full_size_256x256(ctx):
     g30 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=g29[:3], iters=1)
     eta = oracle.step_sizes(hh, n_np.max(), 2, spec.T)
     r30 = oracle.iterate(z_np, n_np, g29[0], g29[1], g29[2], hh, spec.T, spec.rows, spec.cols, p, *eta)
-    compare_state(g30, r30, n_np, 1e-3, 1e-4, FLIP_FRAC, "256x256 iteration 30")
+    compare_state(g30, r30, n_np, 1e-3, 1e-4, FLIP_FRAC, "256x256 iteration 30", spec.T, outlier_frac=1e-4)
     # quality against the synthetic truth: most first surfaces found within 3 sigma
     d = np.abs(g30[0][:, 0] - fr.truth.depth[:, 0])
     assert np.mean(g30[2][:, 0] & (d <= 3 * spec.sigma)) > 0.9
@@ -252,7 +264,7 @@ def test_edge_cases(ctx):
                                    init=oracle.init_matched_filter(to_complex(z), counts(n), hh, T, p)[:3])
             empty = counts(n) == 0
             assert not g[2][empty].any() and np.all(g[3][empty] == 1.0)
-            compare_state(g, r, counts(n), DEPTH_TOL, INTENSITY_RTOL, 0.0, f"edge {rows}x{cols} r={radius}")
+            compare_state(g, r, counts(n), DEPTH_TOL, INTENSITY_RTOL, 0.0, f"edge {rows}x{cols} r={radius}", T)
 
 
 def test_invalid_params_rejected(ctx):
@@ -281,3 +293,24 @@ def test_init_large_and_small_T(ctx, T, m, sigma):
     p = oracle_params(iters=0, k_max=2, d_max=6 * sigma, min_sep=3 * sigma)
     g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, T, m, h32, p)
     check_init_validity(g[0], g[1], g[2], z_np, n_np, hh, T, p)
+
+
+@pytest.mark.parametrize("iters", [1, 2])
+def test_iteration_parity_on_frame_larger_than_one_wave(ctx, iters):
+    # 512 x 384 pixels = 768 tiles of 16 x 16, more than the CTAs resident at
+    # once: tiles of a later wave read their neighbours' halo while earlier
+    # tiles have already finished, so the iteration must not update in place.
+    spec = synth.FrameSpec(rows=384, cols=512, T=1024, sigma=4.0, mean_photons=120.0, sbr=1.0, two_surface_frac=0.1)
+    m = 6
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, 61, m)
+    p = oracle_params(iters=iters, k_max=2, d_max=24.0, min_sep=12.0)
+    s0 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, iters=2)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=s0[:3], iters=iters)
+    eta = oracle.step_sizes(hh, n_np.max(), 2, spec.T)
+    r = (s0[0], s0[1], s0[2], None)
+    for _ in range(iters):
+        r = oracle.iterate(z_np, n_np, r[0], r[1], r[2], hh, spec.T, spec.rows, spec.cols, p, *eta)
+    # a state updated in place would put thousands of points off; decision
+    # flips (e.g. a 3-neighbour plane fit at its acceptance threshold) touch
+    # a handful
+    compare_state(g, r, n_np, 1e-3, 1e-4, FLIP_FRAC, f"{iters} iteration(s), 768 tiles", spec.T, outlier_frac=1e-4)
