@@ -470,6 +470,9 @@ def kernel_work(name, N, P, m, T, K, iters):
         # window, the APSS weight and moments for the normal (~25 instr) and
         # for the sphere and smoothing (~30 instr)
         return "alu", P * K * (14 * m + 9 * K * 55) / 1e12, "Tinst"
+    if name == "iter_all":
+        # all iterations in one launch
+        return "alu", iters * P * K * (14 * m + 9 * K * 55) / 1e12, "Tinst"
     if name == "finalize":
         return "hbm", (P * m * 16 + P * 4) / 1e9, "GB"
     return None, None, None

@@ -79,6 +79,7 @@ enum KernelId : uint32_t {
   KID_INIT,
   KID_GRAD,
   KID_ITER,
+  KID_ITER_ALL,
   KID_ALPHA0,
   KID_BATCH,
   KID_COUNT

@@ -5,7 +5,7 @@ namespace srt3d {
 
 static const char* kKernelNames[KID_COUNT] = {
     "sketch_stream", "finalize", "hist_from_stream", "sketch_hist_fp32", "sketch_hist_tc",
-    "prep",          "init",     "grad",             "iter",             "alpha0",
+    "prep",          "init",     "grad",             "iter",             "iter_all",         "alpha0",
     "batch_graph"};
 
 static cudaEvent_t take_event(Profiler& pf) {

@@ -23,6 +23,7 @@
 // step sizes live in a scratch block.
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -34,7 +35,7 @@ constexpr int kBlock = 256;
 constexpr int kMaxM = 32;
 
 // misc[] slots in the scratch block
-enum { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_COUNT = 8 };
+enum { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_BAR = 4, MISC_COUNT = 8 };
 
 struct Scratch {
   float* t1;
@@ -142,6 +143,8 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
     misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
     misc[MISC_E2] = sa;
     misc[MISC_NMAX] = float(max(s_nmax, 1u));
+    reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
+    reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // grid barrier: generation
   }
 }
 
@@ -604,7 +607,8 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
                                           const float* __restrict__ misc, const float* __restrict__ depth_in,
                                           const float* __restrict__ alpha_in, const uint8_t* __restrict__ active_in,
                                           float* __restrict__ depth, float* __restrict__ alpha,
-                                          uint8_t* __restrict__ active, float* __restrict__ alpha0) {
+                                          uint8_t* __restrict__ active, float* __restrict__ alpha0,
+                                          const float2* s_z = nullptr, const uint32_t* s_nn = nullptr) {
   constexpr int H = 2 * R;
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
   constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
@@ -633,7 +637,10 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
         a[k] = alpha_in[p * K + k];
         act[k] = active_in[p * K + k] != 0;
       }
-      grad_pixel<K>(z + p * m, n[p], T, m, s_hh, eta_t, eta_a, t, a, act);
+      if (s_z)  // the region's sketches, kept in shared memory across iterations
+        grad_pixel<K>(s_z + size_t(i) * m, s_nn[i], T, m, s_hh, eta_t, eta_a, t, a, act);
+      else
+        grad_pixel<K>(z + p * m, n[p], T, m, s_hh, eta_t, eta_a, t, a, act);
     } else {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
@@ -804,6 +811,83 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
                     f.depth_alt, f.alpha_alt, f.active_alt, f.alpha0);
 }
 
+constexpr long long kGridWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident): arrival
+// counter and generation word in global memory, zeroed by k_prep. The wait is
+// bounded: after kGridWaitCycles the CTA latches FLAG_DEVICE_TIMEOUT, marks
+// itself aborted and returns false.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, uint32_t* flags, int* s_abort) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kGridWaitCycles) {
+          *s_abort = 1;
+          atomicOr(flags, FLAG_DEVICE_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *s_abort == 0;
+}
+
+// All iterations in one cooperative launch, one CTA per tile: the tile's
+// region of sketches and counts is loaded into shared memory once; between
+// iterations the state goes through global memory (ping-pong buffers) and a
+// grid barrier.
+template <int K, int R>
+__global__ void __launch_bounds__(iter_threads<R>()) k_iter_persistent(
+    Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
+    const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
+    float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x,
+    uint32_t* __restrict__ flags) {
+  constexpr int H = 2 * R;
+  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
+  constexpr int NT = iter_threads<R>();
+  extern __shared__ float2 s_z[];  // [RH * RW][m] sketches, then [RH * RW] counts
+  uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(RH) * RW * m);
+  __shared__ int s_abort;
+  const uint32_t tile_x = blockIdx.x % tiles_x, tile_y = blockIdx.x / tiles_x;
+  const int r0 = int(tile_y) * kTH - H, c0 = int(tile_x) * kTW - H;
+  for (uint32_t i = threadIdx.x; i < uint32_t(RH * RW) * m; i += NT) {
+    const uint32_t q = i / m, l = i - q * m;
+    const int rr = r0 + int(q) / RW, cc = c0 + int(q) % RW;
+    const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
+    s_z[i] = in ? z[(size_t(rr) * st.cols + size_t(cc)) * m + l] : make_float2(0.f, 0.f);
+  }
+  for (uint32_t q = threadIdx.x; q < uint32_t(RH * RW); q += NT) {
+    const int rr = r0 + int(q) / RW, cc = c0 + int(q) % RW;
+    const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
+    s_nn[q] = in ? n[size_t(rr) * st.cols + size_t(cc)] : 0u;
+  }
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+  unsigned* bar = reinterpret_cast<unsigned*>(misc) + MISC_BAR;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const bool from_alt = ((iters - it) & 1u) != 0;  // the last iteration writes the caller's buffers
+    if (from_alt)
+      iter_tile<K, R>(st, tile_x, tile_y, z, n, T, m, hh_g, misc, alt_d, alt_a, alt_c, depth, alpha, active, alpha0,
+                      s_z, s_nn);
+    else
+      iter_tile<K, R>(st, tile_x, tile_y, z, n, T, m, hh_g, misc, depth, alpha, active, alt_d, alt_a, alt_c, alpha0,
+                      s_z, s_nn);
+    if (it + 1 < iters && !grid_sync(bar, gridDim.x, flags, &s_abort)) break;
+  }
+}
+
 // Copy every frame's state to its alternate buffers (one CTA per tile).
 template <int K>
 __global__ void k_copy_state_batch(const BatchFrame* __restrict__ frames, uint32_t nframes) {
@@ -837,6 +921,43 @@ __global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint
 #pragma unroll
   for (int k = 0; k < K; ++k) s += active[size_t(p) * K + k] ? alpha[size_t(p) * K + k] : 0.f;
   alpha0[p] = 1.f - s;
+}
+
+// Cooperative launch of k_iter_persistent; SRT3D_EAGAIN when the tiles do
+// not all fit on the device at once (the caller then launches per iteration).
+template <int K, int R>
+srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const float2* z, const uint32_t* n,
+                                    uint32_t T, uint32_t m, const Scratch& sc, float* depth, float* alpha,
+                                    uint8_t* active, float* alpha0, uint32_t iters, dim3 tiles,
+                                    cudaStream_t stream) {
+  constexpr int H = 2 * R;
+  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
+  const size_t zsmem = size_t(RH) * RW * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
+  const uint32_t ntiles = tiles.x * tiles.y;
+  auto fn = k_iter_persistent<K, R>;
+  cudaFuncAttributes fa;
+  SRT3D_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, fn));
+  if (fa.sharedSizeBytes + zsmem > ctx->smem_optin) return SRT3D_EAGAIN;
+  // static + dynamic shared memory may exceed the 48 KB default
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
+  int bps = 0;
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, iter_threads<R>(), zsmem));
+  if (uint64_t(bps) * uint64_t(ctx->num_sms) < ntiles) return SRT3D_EAGAIN;
+  Stencil stv = st;
+  const float2* zz = z;
+  const uint32_t* nn = n;
+  uint32_t TT = T, mm = m, it = iters, tx = tiles.x;
+  const float2* hh = sc.hh;
+  float* misc = sc.misc;
+  float *d = depth, *a = alpha, *a0 = alpha0, *ad = sc.t1, *aa = sc.a1;
+  uint8_t *c = active, *ac = sc.act1;
+  uint32_t* flags = ctx->d_flags;
+  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &ad, &aa, &ac, &it, &tx, &flags};
+  const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
+  SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles), dim3(iter_threads<R>()),
+                                                  args, zsmem, stream));
+  prof_end(ctx, KID_ITER_ALL, mk, stream);
+  return SRT3D_OK;
 }
 
 template <int K>
@@ -902,6 +1023,25 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
     SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
     SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
+  }
+  // All iterations in one cooperative launch when every tile's CTA fits on
+  // the device at once (SRT3D_ITER_PERSISTENT=0 forces one launch per iteration).
+  if (prm.regularize && prm.iters > 0) {
+    const char* env = std::getenv("SRT3D_ITER_PERSISTENT");
+    const bool allow = !(env && env[0] == '0');
+    srt3d_status pst = SRT3D_EAGAIN;
+    if (allow) {
+      if (prm.radius == 1)
+        pst = launch_iter_persistent<K, 1>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+                                           stream);
+      else if (prm.radius == 2)
+        pst = launch_iter_persistent<K, 2>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+                                           stream);
+      else
+        pst = launch_iter_persistent<K, 3>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+                                           stream);
+    }
+    if (pst != SRT3D_EAGAIN) return pst;  // launched (or failed)
   }
   for (uint32_t it = 0; it < prm.iters; ++it) {
     const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);

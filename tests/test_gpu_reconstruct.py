@@ -314,3 +314,28 @@ def test_iteration_parity_on_frame_larger_than_one_wave(ctx, iters):
     # flips (e.g. a 3-neighbour plane fit at its acceptance threshold) touch
     # a handful
     compare_state(g, r, n_np, 1e-3, 1e-4, FLIP_FRAC, f"{iters} iteration(s), 768 tiles", spec.T, outlier_frac=1e-4)
+
+
+def test_persistent_and_per_iteration_launches_agree_exactly(ctx, monkeypatch):
+    # The same iteration arithmetic runs as one cooperative launch (all tiles
+    # resident, sketches cached in shared memory, grid barrier between
+    # iterations) or as one launch per iteration; results are bit-identical.
+    spec = synth.FrameSpec(rows=70, cols=90, T=4096, sigma=6.0, mean_photons=400.0, sbr=0.5, two_surface_frac=0.2)
+    m = 10
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, 71, m)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("SRT3D_ITER_PERSISTENT", flag)
+        for iters in (7, 8):
+            p = oracle_params(iters=iters, k_max=2, d_max=36.0, min_sep=18.0)
+            B.srt3d_profile_enable(ctx, True)
+            out.append(gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p))
+            launched = B.profile_totals(ctx)
+            B.srt3d_profile_enable(ctx, False)
+            if flag == "1":
+                assert launched["iter_all"][1] == 1 and "iter" not in launched
+            else:
+                assert launched["iter"][1] == iters and "iter_all" not in launched
+    for a, b in ((out[0], out[2]), (out[1], out[3])):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
