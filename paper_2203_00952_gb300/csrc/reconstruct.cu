@@ -546,6 +546,18 @@ __device__ __forceinline__ float apss_weight(const Stencil& st, float dx, float 
   return u2 * u2;
 }
 
+// Branch-free APSS weight: the same arithmetic as apss_weight, 0 for a slot
+// that is not a neighbour (inactive, beyond d_max, or outside the support).
+__device__ __forceinline__ float slot_weight(const Stencil& st, float dx, float dy, float dt, bool active,
+                                             float& dz, bool& ok) {
+  dz = dt * st.ds;
+  const float d2 = dx * dx + dy * dy + dz * dz;
+  const float u = 1.f - d2 * st.inv_h2;
+  const float u2 = u * u;
+  ok = active && fabsf(dt) <= st.d_max && d2 < st.h2;
+  return ok ? u2 * u2 : 0.f;
+}
+
 // Unit normal from the weighted plane-fit moments (z = a + b x + c y).
 __device__ __forceinline__ float4 plane_normal(int cnt, float Sw, float Sx, float Sy, float Sz, float Sxx, float Sxy,
                                                float Syy, float Sxz, float Syz) {
@@ -668,6 +680,8 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
         const float tq = s_t[q0][k];
         float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
         int cnt = 0;
+        // branch-free: every slot is loaded and weighted (0 for non-neighbours),
+        // which leaves the sums exactly as if the slot were skipped
 #pragma unroll
         for (int dr = -R; dr <= R; ++dr)
 #pragma unroll
@@ -675,11 +689,11 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
             const int q = (lr + dr) * RW + (lc + dc);
 #pragma unroll
             for (int k2 = 0; k2 < K; ++k2) {
-              if (!s_act[q][k2]) continue;
-              float dz;
               const float fx = float(dc), fy = float(dr);
-              const float w = apss_weight(st, fx, fy, s_t[q][k2] - tq, dz);
-              if (w < 0.f) continue;
+              float dz;
+              bool ok;
+              const float w = slot_weight(st, fx, fy, s_t[q][k2] - tq, s_act[q][k2] != 0, dz, ok);
+              cnt += ok ? 1 : 0;
               Sw += w;
               Sx += w * fx;
               Sy += w * fy;
@@ -689,7 +703,6 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
               Syy += w * fy * fy;
               Sxz += w * fx * dz;
               Syz += w * fy * dz;
-              ++cnt;
             }
           }
         nv = plane_normal(cnt, Sw, Sx, Sy, Sz, Sxx, Sxy, Syy, Sxz, Syz);
@@ -724,11 +737,11 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
         const int qn = (lr + dr - R) * NW + (lc + dc - R);
 #pragma unroll
         for (int k2 = 0; k2 < K; ++k2) {
-          if (!s_act[q][k2]) continue;
-          float dz;
           const float fx = float(dc), fy = float(dr);
-          const float w = apss_weight(st, fx, fy, s_t[q][k2] - tq, dz);
-          if (w < 0.f) continue;
+          float dz;
+          bool ok;
+          const float w = slot_weight(st, fx, fy, s_t[q][k2] - tq, s_act[q][k2] != 0, dz, ok);
+          cnt += ok ? 1 : 0;
           const float4 nv = s_n[qn][k2];
           Sw += w;
           Spx += w * fx;
@@ -740,7 +753,6 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
           Spn += w * (fx * nv.x + fy * nv.y + dz * nv.z);
           Spp += w * (fx * fx + fy * fy + dz * dz);
           Swa += w * s_a[q][k2];
-          ++cnt;
         }
       }
     tout[k] = sphere_depth(st, tq, cnt, Sw, Spx, Spy, Spz, Snx, Sny, Snz, Spn, Spp);
