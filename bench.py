@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -454,16 +455,30 @@ def alu_peak_tinst():
     return SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 
 
+def mf_grid_spacing(T, m):
+    """Grid spacing D of the matched-filter branch and bound (largest power
+    of two <= 64 with w_m^2 D^2 / 8 <= 0.02, w_m = 2 pi m / T)."""
+    w = 2.0 * math.pi * m / T
+    D = 64
+    while D > 1 and w * w * D * D / 8.0 > 0.02:
+        D //= 2
+    return D
+
+
 def kernel_work(name, N, P, m, T, K, iters):
     """Algorithmic work of one launch of kernel `name` (per
     photon / pixel / point figures). Returns (bound, amount, unit)."""
     if name == "sketch_stream":
-        # per photon and harmonic: one complex rotation (4 FP32 instr) and two
-        # accumulations; the first harmonic is a table value
-        return "alu", N * (6 * m - 4) / 1e12, "Tinst"
+        # FP32 operations per photon: per harmonic two accumulations and, from
+        # the second harmonic on, one Chebyshev step (one FMA per component)
+        return "alu", N * (4 * m - 2) / 1e12, "Tinst"
     if name == "init":
-        # per pixel, pass and candidate depth: m complex Horner steps (4 FFMA)
-        return "alu", P * K * T * 4 * m / 1e12, "Tinst"
+        # FP32 operations the branch and bound always performs: per pixel and
+        # pass, the score of every grid point t = g D by complex Horner
+        # (4 FMA per harmonic after the first, 2 for the last step); the
+        # point-by-point evaluation of surviving intervals is not counted
+        G = -(-T // mf_grid_spacing(T, m))
+        return "alu", P * K * G * (4 * m - 2) / 1e12, "Tinst"
     if name == "iter":
         # per point and iteration: the gradient step (14 FP32 instr per
         # harmonic per point) and, per neighbour slot of the (2r+1)^2 x K

@@ -4,15 +4,24 @@
 //   k_finalize        z = S / n                                          (Eq. 3)
 //
 // Sketch kernel layout: a group of G lanes (G in {4, 8, 16, 32}) owns one
-// pixel at a time; its lanes read the pixel's stamps as 16-byte words
-// (8 stamps) from an aligned base, so loads are coalesced whatever the
-// pixel's offset. Per photon the exact integer phase x (and (l x) mod T at
-// every 16th harmonic) indexes a shared-memory cos/sin table; the harmonics
-// in between are obtained by complex rotation e_l = e_{l-1} e_1, so the
-// rounding error stays below ~16 (2^-23) per term. Each lane keeps m complex
-// FP32 partial sums; the group reduces them with xor shuffles at the end of
-// the pixel. No floating-point atomics: the result for a pixel does not
-// depend on what else runs.
+// pixel at a time. The pixel's whole 16-byte words (8 stamps, read from an
+// aligned base so loads are coalesced whatever the pixel's offset) are spread
+// over the lanes; the at most 14 stamps of its partial first and last words
+// are taken one per lane in a separate pass, so no lane runs a masked
+// per-stamp path while the others wait. Per photon the exact integer phase x
+// indexes a shared-memory cos/sin table for e_1 = e^{i w_1 x}; higher
+// harmonics follow the Chebyshev recurrence e_j = 2 cos(w_1 x) e_{j-1} -
+// e_{j-2}, run on the signed sequence a_j = s_j e_j (s = +,+,-,-,+,+,...) so
+// that every step is a single packed FMA a_j = (+-2 cos) a_{j-1} + a_{j-2} on
+// the (cos, sin) pair, and a packed add accumulates it. For m > 10 the
+// recurrence restarts from the table (exact index (j x) mod T) every 8
+// harmonics. Rounding error per term: at most 3.5e-6 for m <= 10 and 2.3e-6
+// with restarts (checked exhaustively over x for T from 256 to 8192). For
+// T > 8192 the table is two-level and the harmonics come from complex
+// rotation instead (see add_photon). Each
+// lane keeps m complex FP32 partial sums; the group reduces them with xor
+// shuffles at the end of the pixel. No floating-point atomics: the result for
+// a pixel does not depend on what else runs.
 #include <cmath>
 #include <cstdio>
 
@@ -23,23 +32,54 @@ namespace srt3d {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kResync = 16;  // table lookup every kResync harmonics
+constexpr int kRestart = 8;       // direct table: restart every kRestart harmonics ...
+constexpr int kRestartAbove = 10;  // ... when m exceeds this
+constexpr int kResyncTL = 16;      // two-level table: resync of the rotation
 
-template <int M>
-__device__ __forceinline__ void add_photon(float2 (&acc)[M], uint32_t x, const float2* tab, bool two_level,
-                                           uint32_t T, float invT) {
-  const float2 e1 = phase(tab, x, two_level);
-  float2 e = e1;
-  acc[0].x += e.x;
-  acc[0].y += e.y;
+// acc[j-1] += s_j e^{i w_j x} for j = 1..M, s_j = -1 when j mod 4 is 2 or 3
+// (the caller flips those signs once per pixel). Direct table: Chebyshev
+// recurrence. Two-level table (T > 8192): its composed e_1 carries ~1.5 ulp,
+// which the recurrence would amplify ~j^2-fold, so there the harmonics come
+// from complex rotation e_j = e_{j-1} e_1 (error growing ~j-fold), resynced
+// from the table every 16 harmonics, and the signs are applied per term.
+template <int M, bool TL>
+__device__ __forceinline__ void add_photon(float2 (&acc)[M], uint32_t x, const float2* tab, uint32_t T,
+                                           float invT) {
+  const float2 e1 = phase(tab, x, TL);
+  if (TL) {
+    float2 e = e1;
+    acc[0] = fadd2(acc[0], e);
+#pragma unroll
+    for (int j = 2; j <= M; ++j) {
+      if ((j - 1) % kResyncTL == 0)
+        e = phase(tab, mulmod(uint32_t(j), x, T, invT), true);
+      else
+        e = cmul(e, e1);
+      acc[j - 1] = (j & 2) ? fsub2(acc[j - 1], e) : fadd2(acc[j - 1], e);
+    }
+    return;
+  }
+  const float c2 = e1.x + e1.x;
+  const float2 pc = make_float2(c2, c2), nc = make_float2(-c2, -c2);
+  float2 p = make_float2(1.f, 0.f);  // a_{j-2}
+  float2 q = e1;                     // a_{j-1}
+  acc[0] = fadd2(acc[0], q);
 #pragma unroll
   for (int j = 2; j <= M; ++j) {
-    if ((j - 1) % kResync == 0)
-      e = phase(tab, mulmod(uint32_t(j), x, T, invT), two_level);
-    else
-      e = cmul(e, e1);
-    acc[j - 1].x += e.x;
-    acc[j - 1].y += e.y;
+    float2 r;
+    if (M > kRestartAbove && (j - 1) % kRestart == 0) {
+      // a_{j-1} = e_{j-1}, a_j = e_j from the table (s = + at j - 1 = 0 mod 4 and j)
+      const uint32_t k0 = mulmod(uint32_t(j - 1), x, T, invT);
+      uint32_t k1 = k0 + x;
+      k1 -= (k1 >= T) ? T : 0u;
+      q = phase(tab, k0, false);
+      r = phase(tab, k1, false);
+    } else {
+      r = ffma2((j & 1) ? pc : nc, q, p);
+    }
+    p = q;
+    q = r;
+    acc[j - 1] = fadd2(acc[j - 1], r);
   }
 }
 
@@ -49,6 +89,42 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
                : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                : "l"(p));
   return v;
+}
+
+// All photons of one pixel for lane gl of its group: the loose stamps one
+// per lane, then whole words. Returns whether a stamp was >= T.
+template <int M, bool TL>
+__device__ __forceinline__ bool pixel_photons(float2 (&acc)[M], const uint4* __restrict__ words,
+                                              const uint16_t* __restrict__ half, uint32_t a, uint32_t b,
+                                              uint32_t nh, uint32_t nl, uint32_t ts, uint32_t wa, uint32_t wb,
+                                              uint32_t T, float invT, uint32_t G, uint32_t gl, const float2* s_tab) {
+  bool bad = false;
+  for (uint32_t i = gl; i < nl; i += G) {
+    const uint32_t x = __ldg(half + (i < nh ? a + i : ts + (i - nh)));
+    if (x < T)
+      add_photon<M, TL>(acc, x, s_tab, T, invT);
+    else
+      bad = true;
+  }
+  for (uint32_t w = wa + gl; w < wb; w += G) {
+    const uint4 v = ld_stream(words + w);
+    const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
+                           v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
+    uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
+    if (mx < T) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (x[i] < T)
+          add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+        else
+          bad = true;
+      }
+    }
+  }
+  return bad;
 }
 
 // One pixel of the stream, processed by a group of G lanes: coalesced 16-byte
@@ -69,37 +145,21 @@ __device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, ui
   float2 acc[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) acc[j] = make_float2(0.f, 0.f);
+  // positions relative to the aligned base; whole words [wa, wb), loose
+  // stamps [a, he) and [ts, b)
   const uint32_t a = s + shift, b = e + shift;
-  bool bad = false;
-  for (uint32_t w = (a >> 3) + gl; w < ((b + 7u) >> 3); w += G) {
-    const uint4 v = ld_stream(words + w);
-    const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
-                           v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
-    const uint32_t base = w << 3;
-    uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
-    if (base >= a && base + 8u <= b && mx < T) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) add_photon<M>(acc, x[i], s_tab, tl, T, invT);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const uint32_t idx = base + uint32_t(i);
-        if (idx >= a && idx < b) {
-          if (x[i] < T)
-            add_photon<M>(acc, x[i], s_tab, tl, T, invT);
-          else
-            bad = true;
-        }
-      }
-    }
-  }
+  const uint32_t wa = (a + 7u) >> 3, wb = b >> 3;
+  const uint32_t he = min(b, wa << 3), ts = max(he, wb << 3);
+  const uint32_t nh = he - a, nl = nh + (b - ts);
+  const uint16_t* half = reinterpret_cast<const uint16_t*>(words);
+  const bool bad = tl ? pixel_photons<M, true>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab)
+                      : pixel_photons<M, false>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab);
   if (bad) atomicOr(flags, FLAG_STAMP_RANGE);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    for (uint32_t off = G >> 1; off > 0; off >>= 1) {
-      acc[j].x += __shfl_xor_sync(gmask, acc[j].x, off);
-      acc[j].y += __shfl_xor_sync(gmask, acc[j].y, off);
-    }
+    for (uint32_t off = G >> 1; off > 0; off >>= 1)
+      acc[j] = fadd2(acc[j], make_float2(__shfl_xor_sync(gmask, acc[j].x, off), __shfl_xor_sync(gmask, acc[j].y, off)));
+    if ((j + 1) & 2) acc[j] = make_float2(-acc[j].x, -acc[j].y);
   }
   float2* Sp = S + size_t(p) * m;
 #pragma unroll

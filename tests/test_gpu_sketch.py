@@ -49,6 +49,20 @@ def test_sketch_edge_cases(ctx, T, m, sizes):
     assert sketch_err(S, n, S_ref, n_ref) <= TOL
 
 
+@pytest.mark.parametrize("T,m,bound", [(4096, 10, 4e-6), (4613, 10, 4e-6), (1024, 32, 2.5e-6), (65535, 32, 2.5e-6)])
+def test_sketch_every_phase_single_photon(ctx, T, m, bound):
+    """One photon per pixel, every x in [0, T) once: S[x][l-1] is the single
+    term e^{i 2 pi l x / T} of Eq. 3, so this bounds the per-term rounding of
+    the recurrence between table restarts over all phases."""
+    stamps = np.arange(T, dtype=np.uint16)
+    offsets = np.arange(T + 1, dtype=np.uint32)
+    S, n = gpu_sketch_stream(ctx, stamps, offsets, T, m)
+    B.srt3d_sync(ctx)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, T, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert np.max(np.abs(to_complex(S) - S_ref)) <= bound
+
+
 def test_sketch_unaligned_stream_base(ctx):
     rng = np.random.default_rng(5)
     T, m = 4096, 10
