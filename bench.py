@@ -457,10 +457,10 @@ def alu_peak_tinst():
 
 def mf_grid_spacing(T, m):
     """Grid spacing D of the matched-filter branch and bound (largest power
-    of two <= 64 with w_m^2 D^2 / 8 <= 0.02, w_m = 2 pi m / T)."""
+    of two <= 64 with w_m^2 D^2 / 8 <= 0.08, w_m = 2 pi m / T)."""
     w = 2.0 * math.pi * m / T
     D = 64
-    while D > 1 and w * w * D * D / 8.0 > 0.02:
+    while D > 1 and w * w * D * D / 8.0 > 0.08:
         D //= 2
     return D
 

@@ -171,7 +171,7 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   std::vector<BatchFrame> hf(num_frames);
   std::map<int, std::vector<uint3>> sketch_items;  // by instantiated M
   std::map<int, uint64_t> group_photons;
-  std::vector<uint3> init_items;
+  std::map<int, std::vector<uint3>> init_items;  // by instantiated init M
   uint32_t tiles = 0;
   for (uint32_t i = 0; i < num_frames; ++i)
     group_photons[sketch_round_m(frames[i].m)] += frames[i].num_stamps;
@@ -208,10 +208,11 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     const uint32_t span = uint32_t(std::min<double>(b.P, std::max(32.0, std::ceil(target / mean))));
     for (uint32_t p0 = 0; p0 < b.P; p0 += span) sketch_items[M].push_back(make_uint3(i, p0, std::min(b.P, p0 + span)));
     for (uint32_t p0 = 0; p0 < b.P; p0 += kInitItemPixels)
-      init_items.push_back(make_uint3(i, p0, std::min(b.P, p0 + kInitItemPixels)));
+      init_items[init_round_m(f.m)].push_back(make_uint3(i, p0, std::min(b.P, p0 + kInitItemPixels)));
   }
-  size_t items_total = init_items.size();
+  size_t items_total = 0;
   for (auto& kv : sketch_items) items_total += kv.second.size();
+  for (auto& kv : init_items) items_total += kv.second.size();
   const size_t frames_bytes = al256(num_frames * sizeof(BatchFrame));
   const size_t scratch_per_frame = 512;  // hhat[32] float2 + misc[8] float
   const uint32_t K = params->k_max;
@@ -240,13 +241,19 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     groups.push_back({kv.first, {all_items.size(), kv.second.size()}});
     all_items.insert(all_items.end(), kv.second.begin(), kv.second.end());
   }
-  const size_t init_off = all_items.size();
-  all_items.insert(all_items.end(), init_items.begin(), init_items.end());
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> igroups;  // init M -> (offset, count)
+  for (auto& kv : init_items) {
+    igroups.push_back({kv.first, {all_items.size(), kv.second.size()}});
+    all_items.insert(all_items.end(), kv.second.begin(), kv.second.end());
+  }
   SRT3D_CUDA_TRY(ctx, cudaMemcpy(base, hf.data(), num_frames * sizeof(BatchFrame), cudaMemcpyHostToDevice));
   SRT3D_CUDA_TRY(ctx, cudaMemcpy(base + frames_bytes, all_items.data(), all_items.size() * sizeof(uint3),
                                  cudaMemcpyHostToDevice));
   const BatchFrame* d_frames = reinterpret_cast<const BatchFrame*>(base);
   const uint3* d_items = reinterpret_cast<const uint3*>(base + frames_bytes);
+  std::vector<InitGroup> init_groups;
+  for (auto& g : igroups)
+    init_groups.push_back({g.first, d_items + g.second.first, uint32_t(g.second.second)});
   // ---------------------------------------------------------------- capture
   if (!cache->capture) SRT3D_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cache->capture, cudaStreamNonBlocking));
   cudaStream_t cs = cache->capture;
@@ -261,7 +268,7 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   }
   if (st == SRT3D_OK) st = launch_finalize_batch(ctx, d_frames, num_frames, max_pm, cs);
   if (st == SRT3D_OK)
-    st = launch_reconstruct_batch(ctx, d_frames, num_frames, d_items + init_off, uint32_t(init_items.size()),
+    st = launch_reconstruct_batch(ctx, d_frames, num_frames, init_groups.data(), uint32_t(init_groups.size()),
                                   tiles, max_entries, max_G, *params, cs);
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(cs, &graph);

@@ -68,6 +68,10 @@ struct BatchFrame {
   uint32_t tiles_x;  // iteration tiles per row
 };
 
+// Slots of the per-frame reconstruction scalars (misc[]): step sizes, E2 =
+// sum |hhat|^2, n_max, and two words of the persistent kernel's grid barrier.
+enum : uint32_t { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_BAR = 4, MISC_COUNT = 8 };
+
 // Kernel ids for the profiling counters.
 enum KernelId : uint32_t {
   KID_SKETCH_STREAM = 0,
@@ -143,10 +147,26 @@ srt3d_status launch_sketch_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, con
                                  uint32_t num_items, int M, uint32_t max_tab_entries, cudaStream_t stream);
 srt3d_status launch_finalize_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
                                    uint32_t max_pm, cudaStream_t stream);
+// Init work items of one instantiated harmonic count M (see init_round_m).
+struct InitGroup {
+  int M;
+  const uint3* items;
+  uint32_t count;
+};
 srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
-                                      const uint3* d_init_items, uint32_t num_init_items, uint32_t total_tiles,
+                                      const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
                                       uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
                                       cudaStream_t stream);
+// Matched-filter initialisation (init.cu): hh = hhat[m], misc = frame scalars.
+srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
+                         uint32_t K, const PhaseTable& tab, const float2* hh, const float* misc,
+                         const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
+                         cudaStream_t stream);
+// Batched: every frame of the items has m <= M, M an instantiated count.
+srt3d_status launch_init_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const uint3* d_items,
+                               uint32_t num_items, uint32_t K, int M, uint32_t max_entries, uint32_t max_G,
+                               const srt3d_params& prm, cudaStream_t stream);
+int init_round_m(uint32_t m);
 uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m);
 srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                      uint64_t num_stamps, uint32_t P, uint32_t T, uint16_t* hist,

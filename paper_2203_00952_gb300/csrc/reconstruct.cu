@@ -6,10 +6,7 @@
 // with up to K = 2 points (t_k, alpha_k):
 //   k_prep    hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau} (Eq. 4), the global
 //             step sizes, and n_max
-//   k_init    sketched matched filter: argmax over integer t of
-//             Re sum_l conj(hhat_l e^{i w_l t}) z_l (Horner in w = e^{-i 2pi t/T},
-//             exact branch and bound on a coarse grid), alpha = s / sum|hhat|^2,
-//             second surface from the residual
+//   k_init    sketched matched filter (init.cu)
 //   per iteration, one fused tile kernel (k_iter):
 //             Jacobi gradient step on n ||z - Psi||^2 (t, alpha), alpha >= 0,
 //             sum alpha <= 1; weighted least-squares plane normals over the
@@ -33,9 +30,6 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kMaxM = 32;
-
-// misc[] slots in the scratch block
-enum { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_BAR = 4, MISC_COUNT = 8 };
 
 struct Scratch {
   float* t1;
@@ -163,277 +157,6 @@ __global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restric
   prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc, s_tab);
 }
 
-// Matched-filter score s(t) = Re sum_{l=1}^{m} c_l w^l for w = e^{-i 2 pi t / T},
-// by complex Horner (4 FFMA per harmonic). `we` is e^{+i 2 pi t / T}.
-__device__ __forceinline__ float mf_score(const float2* c, uint32_t m, float2 we) {
-  const float2 w = make_float2(we.x, -we.y);
-  float ax = c[m - 1].x, ay = c[m - 1].y;
-  for (int l = int(m) - 2; l >= 0; --l) {
-    const float nx = fmaf(ax, w.x, fmaf(-ay, w.y, c[l].x));
-    const float ny = fmaf(ax, w.y, fmaf(ay, w.x, c[l].y));
-    ax = nx;
-    ay = ny;
-  }
-  return fmaf(ax, w.x, -ay * w.y);
-}
-
-__device__ __forceinline__ bool mf_allowed(uint32_t t, int excl_t, float min_sep, uint32_t T) {
-  if (excl_t < 0) return true;
-  const uint32_t d0 = t > uint32_t(excl_t) ? t - uint32_t(excl_t) : uint32_t(excl_t) - t;
-  return float(min(d0, T - d0)) >= min_sep;
-}
-
-__device__ __forceinline__ void mf_take(float s, uint32_t t, float& bs, uint32_t& bt) {
-  if (s > bs || (s == bs && t < bt)) {
-    bs = s;
-    bt = t;
-  }
-}
-
-// Grid spacing of the branch and bound for a frame: the largest power of two
-// D <= 64 with w_m^2 D^2 / 8 <= 0.02, so that for every pixel the curvature
-// term M2 D^2 / 8 stays below 2% of M0 (M2 <= w_m^2 M0). G = ceil(T / D) is
-// then at most 1024.
-uint32_t mf_grid_spacing_impl(uint32_t T, uint32_t m) {
-  const double w = 2.0 * M_PI * double(m) / double(T);
-  uint32_t D = 64u;
-  while (D > 1u && w * w * double(D) * double(D) / 8.0 > 0.02) D >>= 1;
-  return D;
-}
-
-// Exact argmax over integer t in [0, T) (smallest t on ties) of the FP32
-// scores, one warp per pixel, by branch and bound: s is a trigonometric
-// polynomial with |s''| <= M2 = sum_l |c_l| w_l^2, so on an interval of length
-// L between grid points s <= max(endpoints) + M2 L^2 / 8. Scores are evaluated
-// on the grid t = g D (phases from the conflict-free coarse table s_wg, scores
-// kept in s_grid), and only intervals whose bound (plus a margin covering the
-// FP32 evaluation error of both ends) reaches the best grid score are
-// evaluated point by point. Every t whose FP32 score can be the maximum is
-// evaluated with the same arithmetic as an exhaustive scan, so the result
-// equals the exhaustive FP32 argmax.
-__device__ __forceinline__ void warp_argmax_scores(const float2* c, uint32_t m, uint32_t T, const float2* s_tab,
-                                                   bool tl, const float2* s_wg, float* s_grid, uint32_t D,
-                                                   uint32_t G, int excl_t, float min_sep, float* best_s,
-                                                   uint32_t* best_t) {
-  const uint32_t lane = threadIdx.x & 31u;
-  float m0 = 0.f, m2 = 0.f;
-  for (uint32_t l = lane; l < m; l += 32u) {
-    const float a = sqrtf(c[l].x * c[l].x + c[l].y * c[l].y);
-    const float w = 6.283185307179586f * float(l + 1u) / float(T);
-    m0 += a;
-    m2 += a * w * w;
-  }
-  for (int off = 16; off; off >>= 1) {
-    m0 += __shfl_xor_sync(0xffffffffu, m0, off);
-    m2 += __shfl_xor_sync(0xffffffffu, m2, off);
-  }
-  if (m0 == 0.f) {  // all scores are exactly 0: the smallest allowed t wins
-    for (uint32_t t0 = 0; t0 < T; t0 += 32u) {
-      const uint32_t t = t0 + lane;
-      const unsigned ok = __ballot_sync(0xffffffffu, t < T && mf_allowed(t, excl_t, min_sep, T));
-      if (ok) {
-        *best_s = 0.f;
-        *best_t = t0 + uint32_t(__ffs(ok)) - 1u;
-        return;
-      }
-    }
-    *best_s = -FLT_MAX;
-    *best_t = 0xffffffffu;
-    return;
-  }
-  m2 *= 1.01f;
-  const float margin = 4e-5f * m0 + 1e-30f;
-  float bs = -FLT_MAX;
-  uint32_t bt = 0xffffffffu;
-  // grid points (every score kept: the interval bounds need them)
-  for (uint32_t g = lane; g < G; g += 32u) {
-    const float sg = mf_score(c, m, s_wg[g]);
-    s_grid[g] = sg;
-    if (mf_allowed(g * D, excl_t, min_sep, T)) mf_take(sg, g * D, bs, bt);
-  }
-  __syncwarp();
-  float best_grid = bs;
-  for (int off = 16; off; off >>= 1) best_grid = fmaxf(best_grid, __shfl_xor_sync(0xffffffffu, best_grid, off));
-  // intervals whose bound reaches the best grid score
-  if (D > 1u) {
-    for (uint32_t base = 0; base < G; base += 32u) {
-      const uint32_t i = base + lane;
-      bool surv = false;
-      if (i < G) {
-        const uint32_t len = min(D, T - i * D);
-        if (len > 1u) {
-          const float sa = s_grid[i], sb = s_grid[i + 1u < G ? i + 1u : 0u];
-          surv = fmaxf(sa, sb) + m2 * float(len * len) * 0.125f + margin >= best_grid;
-        }
-      }
-      unsigned mask = __ballot_sync(0xffffffffu, surv);
-      while (mask) {
-        const uint32_t j = uint32_t(__ffs(mask)) - 1u;
-        mask &= mask - 1u;
-        const uint32_t a = (base + j) * D;
-        const uint32_t len = min(D, T - a);
-        for (uint32_t t = a + 1u + lane; t < a + len; t += 32u) {
-          if (!mf_allowed(t, excl_t, min_sep, T)) continue;
-          mf_take(mf_score(c, m, phase(s_tab, t, tl)), t, bs, bt);
-        }
-      }
-    }
-  }
-  __syncwarp();
-  for (int off = 16; off; off >>= 1) {
-    const float os = __shfl_xor_sync(0xffffffffu, bs, off);
-    const uint32_t ot = __shfl_xor_sync(0xffffffffu, bt, off);
-    mf_take(os, ot, bs, bt);
-  }
-  *best_s = bs;
-  *best_t = bt;
-}
-
-// Matched-filter initialisation of pixel p by one warp (see warp_argmax_scores).
-template <int K>
-__device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict__ z, const uint32_t* __restrict__ n,
-                                           uint32_t T, uint32_t m, const float2* s_tab, bool tl,
-                                           const float2* s_wg, float* s_grid, uint32_t D, uint32_t G,
-                                           const float2* s_hh, float E2, float prune_alpha, float min_sep,
-                                           float2* c, float* __restrict__ depth, float* __restrict__ alpha,
-                                           uint8_t* __restrict__ active, float* __restrict__ alpha0) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const float invT = 1.0f / float(T);
-  const uint32_t cnt = n[p];
-  if (lane < m) {
-    const float2 zl = z[size_t(p) * m + lane];
-    const float2 hc = make_float2(s_hh[lane].x, -s_hh[lane].y);
-    c[lane] = cmul(hc, zl);
-  }
-  __syncwarp();
-  float s1;
-  uint32_t t1;
-  warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, -1, 0.f, &s1, &t1);
-  if (t1 >= T) {  // no finite score (cannot happen for finite z)
-    t1 = 0u;
-    s1 = 0.f;
-  }
-  float a[K], t[K];
-  bool act[K];
-  a[0] = fmaxf(0.f, s1 / E2);
-  t[0] = float(t1);
-  act[0] = (a[0] >= prune_alpha) && cnt > 0;
-  if (K == 2) {
-    __syncwarp();
-    if (lane < m) {
-      const float2 zl = z[size_t(p) * m + lane];
-      const float2 hv = s_hh[lane];
-      const float2 e = phase(s_tab, mulmod(lane + 1u, t1, T, invT), tl);
-      const float f = (a[0] >= prune_alpha) ? a[0] : 0.f;
-      const float2 fit = cmul(hv, e);
-      const float2 r = make_float2(zl.x - f * fit.x, zl.y - f * fit.y);
-      c[lane] = cmul(make_float2(hv.x, -hv.y), r);
-    }
-    __syncwarp();
-    float s2;
-    uint32_t t2;
-    warp_argmax_scores(c, m, T, s_tab, tl, s_wg, s_grid, D, G, int(t1), min_sep, &s2, &t2);
-    if (t2 >= T) {
-      t2 = 0u;
-      s2 = 0.f;
-    }
-    a[K - 1] = fmaxf(0.f, s2 / E2);
-    t[K - 1] = float(t2);
-    act[K - 1] = (a[K - 1] >= prune_alpha) && cnt > 0;
-  }
-  float sum = 0.f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (!act[k]) a[k] = 0.f;
-    sum += a[k];
-  }
-  if (sum > 1.f) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
-    sum = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) sum += a[k];
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      depth[size_t(p) * K + k] = t[k];
-      alpha[size_t(p) * K + k] = a[k];
-      active[size_t(p) * K + k] = act[k] ? 1 : 0;
-    }
-    alpha0[p] = 1.f - sum;
-  }
-  __syncwarp();
-}
-
-// Matched-filter initialisation, one warp per pixel. Dynamic shared memory:
-// the phase table, the coarse table e^{i 2 pi g D / T} (G entries) and one
-// row of G grid scores per warp.
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
-                                                 uint32_t P, uint32_t T, uint32_t m,
-                                                 const float2* __restrict__ table, uint32_t entries,
-                                                 int two_level, uint32_t D, const float2* __restrict__ hh_g,
-                                                 const float* __restrict__ misc, float prune_alpha, float min_sep,
-                                                 float* __restrict__ depth, float* __restrict__ alpha,
-                                                 uint8_t* __restrict__ active, float* __restrict__ alpha0) {
-  extern __shared__ float2 s_tab[];
-  __shared__ float2 s_c[kBlock / 32][kMaxM];
-  __shared__ float2 s_hh[kMaxM];
-  const uint32_t G = (T + D - 1u) / D;
-  float2* s_wg = s_tab + entries;
-  float* s_grid_all = reinterpret_cast<float*>(s_wg + G);
-  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
-  const bool tl = two_level != 0;
-  for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_tab[i] = table[i];
-  __syncthreads();
-  for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * D, tl);
-  __syncthreads();
-  const uint32_t warp = threadIdx.x >> 5;
-  const uint32_t wpb = blockDim.x >> 5;
-  const float E2 = misc[MISC_E2];
-  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb)
-    init_pixel<K>(p, z, n, T, m, s_tab, tl, s_wg, s_grid_all + warp * G, D, G, s_hh, E2, prune_alpha, min_sep,
-                  s_c[warp], depth, alpha, active, alpha0);
-}
-
-// Batched initialisation: items (frame, first pixel, last pixel); the CTA
-// reloads the tables when the frame changes. Dynamic shared memory is sized
-// for the largest frame of the batch.
-template <int K>
-__global__ void __launch_bounds__(kBlock) k_init_batch(const BatchFrame* __restrict__ frames,
-                                                       const uint3* __restrict__ items, uint32_t num_items,
-                                                       uint32_t max_entries, uint32_t max_G, float prune_alpha,
-                                                       float min_sep) {
-  extern __shared__ float2 s_tab[];
-  __shared__ float2 s_c[kBlock / 32][kMaxM];
-  __shared__ float2 s_hh[kMaxM];
-  float2* s_wg = s_tab + max_entries;
-  float* s_grid_all = reinterpret_cast<float*>(s_wg + max_G);
-  const uint32_t warp = threadIdx.x >> 5;
-  const uint32_t wpb = blockDim.x >> 5;
-  uint32_t cur = 0xffffffffu;
-  for (uint32_t it = blockIdx.x; it < num_items; it += gridDim.x) {
-    const uint3 item = items[it];
-    const BatchFrame& f = frames[item.x];
-    const uint32_t G = (f.T + f.D - 1u) / f.D;
-    const bool tl = f.two_level != 0;
-    if (item.x != cur) {
-      __syncthreads();
-      if (threadIdx.x < f.m) s_hh[threadIdx.x] = f.hh[threadIdx.x];
-      for (uint32_t i = threadIdx.x; i < f.tab_entries; i += blockDim.x) s_tab[i] = f.table[i];
-      __syncthreads();
-      for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * f.D, tl);
-      __syncthreads();
-      cur = item.x;
-    }
-    const float E2 = f.misc[MISC_E2];
-    for (uint32_t p = item.y + warp; p < item.z; p += wpb)
-      init_pixel<K>(p, f.S, f.n, f.T, f.m, s_tab, tl, s_wg, s_grid_all + warp * max_G, f.D, G, s_hh, E2, prune_alpha,
-                    min_sep, s_c[warp], f.depth, f.alpha, f.active, f.alpha0);
-  }
-}
-
 // Sketched gradient step (Jacobi) of one pixel's K points: reads the state
 // (t, a, act), returns the post-step (t, a); inactive points keep t, get a = 0.
 template <int K>
@@ -534,20 +257,10 @@ struct Stencil {
   float h2, inv_h2, d_max, ds, lambda, prune_alpha;
 };
 
-// APSS weight of a neighbour at pixel offset (dx, dy) and depth offset dt
-// (bins), or a negative value when it is not a neighbour.
-__device__ __forceinline__ float apss_weight(const Stencil& st, float dx, float dy, float dt, float& dz) {
-  if (fabsf(dt) > st.d_max) return -1.f;
-  dz = dt * st.ds;
-  const float d2 = dx * dx + dy * dy + dz * dz;
-  if (d2 >= st.h2) return -1.f;
-  const float u = 1.f - d2 * st.inv_h2;
-  const float u2 = u * u;
-  return u2 * u2;
-}
-
-// Branch-free APSS weight: the same arithmetic as apss_weight, 0 for a slot
-// that is not a neighbour (inactive, beyond d_max, or outside the support).
+// APSS weight (1 - d^2/h^2)^4 of a neighbour slot at pixel offset (dx, dy)
+// and depth offset dt (bins), computed branch-free: 0 (and ok = false) for a
+// slot that is not a neighbour (inactive, beyond d_max, or outside the
+// support).
 __device__ __forceinline__ float slot_weight(const Stencil& st, float dx, float dy, float dt, bool active,
                                              float& dz, bool& ok) {
   dz = dt * st.ds;
@@ -988,25 +701,9 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   if (prm.init_mode == SRT3D_INIT_MATCHED) {
-    const uint32_t D = mf_grid_spacing_impl(T, m);
-    const uint32_t G = (T + D - 1u) / D;
-    const size_t init_smem = tab_smem + size_t(G) * sizeof(float2) + size_t(kBlock / 32) * G * sizeof(float);
-    if (init_smem > 48 * 1024)
-      SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               int(init_smem)));
-    int bps = 0;
-    SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init<K>, kBlock, init_smem));
-    if (bps < 1) bps = 1;
-    const uint32_t wpb = kBlock / 32;
-    const uint64_t need = (uint64_t(P) + wpb - 1) / wpb;
-    const uint32_t grid = uint32_t(std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps));
-    {
-      const ProfMark mk = prof_begin(ctx, KID_INIT, stream);
-      k_init<K><<<grid, kBlock, init_smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tl, D, sc.hh, sc.misc,
-                                                   prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
-      prof_end(ctx, KID_INIT, mk, stream);
-    }
-    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+    const srt3d_status st = launch_init(ctx, z, n, P, T, m, K, tab, sc.hh, sc.misc, prm, depth, alpha, active,
+                                        alpha0, stream);
+    if (st != SRT3D_OK) return st;
   } else {
     {
       const ProfMark mk = prof_begin(ctx, KID_ALPHA0, stream);
@@ -1083,8 +780,8 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
 }
 
 template <int K>
-srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const uint3* d_items,
-                       uint32_t num_items, uint32_t total_tiles, uint32_t max_entries, uint32_t max_G,
+srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const InitGroup* groups,
+                       uint32_t num_groups, uint32_t total_tiles, uint32_t max_entries, uint32_t max_G,
                        const srt3d_params& prm, cudaStream_t stream) {
   const size_t tab_smem = size_t(max_entries) * sizeof(float2);
   if (tab_smem > 48 * 1024)
@@ -1096,21 +793,11 @@ srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nfra
     prof_end(ctx, KID_PREP, mk, stream);
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
-  const size_t init_smem = tab_smem + size_t(max_G) * sizeof(float2) + size_t(kBlock / 32) * max_G * sizeof(float);
-  if (init_smem > 48 * 1024)
-    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_init_batch<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(init_smem)));
-  int bps = 0;
-  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_init_batch<K>, kBlock, init_smem));
-  if (bps < 1) bps = 1;
-  const uint32_t grid = std::min<uint32_t>(num_items, uint32_t(ctx->num_sms) * uint32_t(bps));
-  {
-    const ProfMark mk = prof_begin(ctx, KID_INIT, stream);
-    k_init_batch<K><<<grid, kBlock, init_smem, stream>>>(d_frames, d_items, num_items, max_entries, max_G,
-                                                        prm.prune_alpha, prm.min_sep);
-    prof_end(ctx, KID_INIT, mk, stream);
+  for (uint32_t g = 0; g < num_groups; ++g) {
+    const srt3d_status st = launch_init_batch(ctx, d_frames, groups[g].items, groups[g].count, K, groups[g].M,
+                                              max_entries, max_G, prm, stream);
+    if (st != SRT3D_OK) return st;
   }
-  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   Stencil st;
   st.rows = 0;
   st.cols = 0;
@@ -1144,17 +831,15 @@ srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nfra
 
 }  // namespace
 
-uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m) { return mf_grid_spacing_impl(T, m); }
-
 srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
-                                      const uint3* d_init_items, uint32_t num_init_items, uint32_t total_tiles,
+                                      const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
                                       uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
                                       cudaStream_t stream) {
   if (prm.k_max == 1)
-    return run_batch<1>(ctx, d_frames, nframes, d_init_items, num_init_items, total_tiles, max_tab_entries, max_G,
-                        prm, stream);
-  return run_batch<2>(ctx, d_frames, nframes, d_init_items, num_init_items, total_tiles, max_tab_entries, max_G,
-                      prm, stream);
+    return run_batch<1>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                        stream);
+  return run_batch<2>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                      stream);
 }
 
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
