@@ -87,8 +87,10 @@ typedef struct srt3d_params {
   int32_t regularize;  /* 1: SRT3D (APSS + intensity smoothing);
                           0: pixelwise sketched estimate (no spatial prior)  */
   float apss_h;        /* APSS weight support, pixel pitches                 */
-  float d_max;         /* neighbour depth gate and largest APSS move, bins   */
-  float depth_scale;   /* pixel pitches per time bin in point coordinates    */
+  float d_max;         /* neighbour depth gate and largest APSS move, bins,
+                          in (0, 1e6]                                         */
+  float depth_scale;   /* pixel pitches per time bin in point coordinates,
+                          in (0, 1e3]                                         */
   float prune_alpha;   /* a point with alpha below this is removed           */
   float smooth_lambda; /* intensity smoothing weight in [0, 1]               */
   float min_sep;       /* init: least circular separation of 2 surfaces, bins */

@@ -82,7 +82,8 @@ srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint3
   if (prm->radius < 1 || prm->radius > 3) return set_error(ctx, SRT3D_EINVAL, "radius must be 1..3");
   if (prm->init_mode != SRT3D_INIT_MATCHED && prm->init_mode != SRT3D_INIT_GIVEN)
     return set_error(ctx, SRT3D_EINVAL, "unknown init_mode");
-  if (!(prm->apss_h > 0.f) || !(prm->d_max > 0.f) || !(prm->depth_scale > 0.f) ||
+  if (!(prm->apss_h > 0.f) || !(prm->d_max > 0.f && prm->d_max <= 1e6f) ||
+      !(prm->depth_scale > 0.f && prm->depth_scale <= 1e3f) ||
       !(prm->prune_alpha >= 0.f) || !(prm->smooth_lambda >= 0.f && prm->smooth_lambda <= 1.f) ||
       !(prm->min_sep >= 0.f))
     return set_error(ctx, SRT3D_EINVAL, "invalid float parameter");

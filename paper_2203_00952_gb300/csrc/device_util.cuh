@@ -50,6 +50,18 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
   return d;
 }
 
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 // (j * x) mod T, exact for j * x < 2^24: the product is exact in float, the
 // float quotient is within 1 of floor(j x / T), and one correction fixes it.
 __device__ __forceinline__ uint32_t mulmod(uint32_t j, uint32_t x, uint32_t T, float invT) {

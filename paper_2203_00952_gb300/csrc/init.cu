@@ -28,18 +28,6 @@ constexpr int kMaxM = 32;
 // the next one up.
 constexpr int kInitM[] = {2, 4, 6, 8, 10, 12, 16, 20, 24, 32};
 
-__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
-  float2 d;
-  asm("{.reg .b64 ra, rb, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\t"
-      "mov.b64 rb, {%4, %5};\n\t"
-      "mul.rn.f32x2 rd, ra, rb;\n\t"
-      "mov.b64 {%0, %1}, rd;}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-  return d;
-}
-
 // The coefficients are held as duplicated pairs (c, c) so that the packed
 // evaluation below can use them directly.
 // s(t) for one t; `we` = e^{+i 2 pi t / T}, so w = conj(we).

@@ -21,6 +21,8 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdlib>
+#include <type_traits>
+#include <utility>
 
 #include "device_util.cuh"
 #include "internal.h"
@@ -311,6 +313,120 @@ __device__ __forceinline__ float sphere_depth(const Stencil& st, float tq, int c
   return tq;
 }
 
+// Calls f(dr, dc) for every offset of the (2R+1)^2 window, rows outer, as
+// compile-time constants (std::integral_constant).
+template <int R, typename F, int... I>
+__device__ __forceinline__ void static_for_window_impl(F& f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I / (2 * R + 1) - R>{}, std::integral_constant<int, I % (2 * R + 1) - R>{}), ...);
+}
+
+template <int R, typename F>
+__device__ __forceinline__ void static_for_window(F& f) {
+  static_for_window_impl<R>(f, std::make_integer_sequence<int, (2 * R + 1) * (2 * R + 1)>{});
+}
+
+// Depth stored for an inactive point in the masked copy: its offset to any
+// depth in [0, T) exceeds every admissible d_max, so the neighbour test
+// rejects it without a separate activity check, and its squared distance
+// (depth_scale <= 1e3) stays finite, so a zero weight times it is zero.
+constexpr float kMaskedDepth = 1e12f;
+
+// The weights of the two points (K = 2) of one neighbour pixel at offset
+// (dc, dr), as a packed pair: the same arithmetic as slot_weight.
+template <int DR, int DC>
+__device__ __forceinline__ float2 slot_weight_pair(const Stencil& st, float2 tm, float2 tq2, float2& dz, float2& d2,
+                                                   int& cnt) {
+  constexpr float c = float(DC * DC + DR * DR);
+  const float2 dt = fsub2(tm, tq2);
+  dz = fmul2(dt, make_float2(st.ds, st.ds));
+  d2 = ffma2(dz, dz, make_float2(c, c));
+  const float2 u = ffma2(d2, make_float2(-st.inv_h2, -st.inv_h2), make_float2(1.f, 1.f));
+  const float2 u2 = fmul2(u, u);
+  const float2 w4 = fmul2(u2, u2);
+  const bool ok0 = fabsf(dt.x) <= st.d_max && d2.x < st.h2;
+  const bool ok1 = fabsf(dt.y) <= st.d_max && d2.y < st.h2;
+  cnt += int(ok0) + int(ok1);
+  return make_float2(ok0 ? w4.x : 0.f, ok1 ? w4.y : 0.f);
+}
+
+// acc + D v for a compile-time integer D (exact for |D| <= 1; an FMA by D
+// otherwise, as the scalar w * fx would round).
+template <int D>
+__device__ __forceinline__ float2 add_scaled(float2 acc, float2 v) {
+  if constexpr (D == 0) return acc;
+  if constexpr (D == 1) return fadd2(acc, v);
+  if constexpr (D == -1) return fsub2(acc, v);
+  return ffma2(v, make_float2(float(D), float(D)), acc);
+}
+
+// Plane-fit normal of point (lr, lc, k) of a K = 2 region from its
+// (2R+1)^2 x 2 neighbour slots, the two points of a neighbour pixel packed.
+template <int R>
+__device__ __forceinline__ float4 normal_pair(const Stencil& st, const float (*s_tm)[2], int RW, int lr, int lc,
+                                              float tq) {
+  const float2 tq2 = make_float2(tq, tq);
+  float2 Sw = make_float2(0.f, 0.f), Sx = Sw, Sy = Sw, Sz = Sw, Sxx = Sw, Sxy = Sw, Syy = Sw, Sxz = Sw, Syz = Sw;
+  int cnt = 0;
+  const auto slot = [&](auto dr_c, auto dc_c) {
+    constexpr int DR = decltype(dr_c)::value, DC = decltype(dc_c)::value;
+    const int q = (lr + DR) * RW + (lc + DC);
+    const float2 tm = *reinterpret_cast<const float2*>(&s_tm[q][0]);
+    float2 dz, d2;
+    const float2 w = slot_weight_pair<DR, DC>(st, tm, tq2, dz, d2, cnt);
+    const float2 wz = fmul2(w, dz);
+    Sw = fadd2(Sw, w);
+    Sz = fadd2(Sz, wz);
+    Sx = add_scaled<DC>(Sx, w);
+    Sy = add_scaled<DR>(Sy, w);
+    Sxx = add_scaled<DC * DC>(Sxx, w);
+    Syy = add_scaled<DR * DR>(Syy, w);
+    Sxy = add_scaled<DC * DR>(Sxy, w);
+    Sxz = add_scaled<DC>(Sxz, wz);
+    Syz = add_scaled<DR>(Syz, wz);
+  };
+  static_for_window<R>(slot);
+  return plane_normal(cnt, Sw.x + Sw.y, Sx.x + Sx.y, Sy.x + Sy.y, Sz.x + Sz.y, Sxx.x + Sxx.y, Sxy.x + Sxy.y,
+                      Syy.x + Syy.y, Sxz.x + Sxz.y, Syz.x + Syz.y);
+}
+
+// Sphere projection and smoothed intensity of point (lr, lc) with depth tq
+// and intensity aq of a K = 2 region (the two points of a neighbour pixel
+// packed). Returns the new depth; *an = the smoothed intensity.
+template <int R>
+__device__ __forceinline__ float project_pair(const Stencil& st, const float (*s_tm)[2], const float (*s_a)[2],
+                                              const float2* s_nx, const float2* s_ny, const float2* s_nz, int RW,
+                                              int NW, int lr, int lc, float tq, float aq, float* an) {
+  const float2 tq2 = make_float2(tq, tq);
+  float2 Sw = make_float2(0.f, 0.f), Spx = Sw, Spy = Sw, Spz = Sw, Snx = Sw, Sny = Sw, Snz = Sw, Spn = Sw,
+         Spp = Sw, Swa = Sw;
+  int cnt = 0;
+  const auto slot = [&](auto dr_c, auto dc_c) {
+    constexpr int DR = decltype(dr_c)::value, DC = decltype(dc_c)::value;
+    const int q = (lr + DR) * RW + (lc + DC);
+    const int qn = (lr + DR - R) * NW + (lc + DC - R);
+    const float2 tm = *reinterpret_cast<const float2*>(&s_tm[q][0]);
+    float2 dz, d2;
+    const float2 w = slot_weight_pair<DR, DC>(st, tm, tq2, dz, d2, cnt);
+    const float2 nx = s_nx[qn], ny = s_ny[qn], nz = s_nz[qn];
+    Sw = fadd2(Sw, w);
+    Spx = add_scaled<DC>(Spx, w);
+    Spy = add_scaled<DR>(Spy, w);
+    Spz = ffma2(w, dz, Spz);
+    Snx = ffma2(w, nx, Snx);
+    Sny = ffma2(w, ny, Sny);
+    Snz = ffma2(w, nz, Snz);
+    const float2 pn = add_scaled<DR>(add_scaled<DC>(fmul2(dz, nz), nx), ny);
+    Spn = ffma2(w, pn, Spn);
+    Spp = ffma2(w, d2, Spp);
+    Swa = ffma2(w, *reinterpret_cast<const float2*>(&s_a[q][0]), Swa);
+  };
+  static_for_window<R>(slot);
+  const float sw = Sw.x + Sw.y;
+  *an = (1.f - st.lambda) * aq + st.lambda * ((Swa.x + Swa.y) / sw);
+  return sphere_depth(st, tq, cnt, sw, Spx.x + Spx.y, Spy.x + Spy.y, Spz.x + Spz.y, Snx.x + Snx.y, Sny.x + Sny.y,
+                      Snz.x + Snz.y, Spn.x + Spn.y, Spp.x + Spp.y);
+}
+
 // One SRT3D iteration on a TW x TH tile, fused: the gradient step on the tile
 // plus a 2R halo, plane-fit normals on the tile plus an R halo, then the
 // sphere projection, intensity smoothing and pruning on the tile. The
@@ -338,10 +454,15 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
   constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
   __shared__ float s_t[RH * RW][K];
-  __shared__ float s_a[RH * RW][K];
+  __shared__ __align__(8) float s_a[RH * RW][K];
   __shared__ uint8_t s_act[RH * RW][K];
+  __shared__ __align__(8) float s_tm[RH * RW][K];  // depth, or kMaskedDepth for an inactive point
   __shared__ float4 s_n[NH * NW][K];
   __shared__ float2 s_hh[kMaxM];
+  // K = 2: normals as component pairs (point 0, point 1) in the same storage
+  float2* s_nx = reinterpret_cast<float2*>(&s_n[0][0]);
+  float2* s_ny = s_nx + NH * NW;
+  float2* s_nz = s_ny + NH * NW;
   const int tid = threadIdx.x;
   if (tid < int(m)) s_hh[tid] = hh_g[tid];
   __syncthreads();
@@ -379,10 +500,25 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
       s_t[i][k] = t[k];
       s_a[i][k] = a[k];
       s_act[i][k] = act[k] ? 1 : 0;
+      s_tm[i][k] = act[k] ? t[k] : kMaskedDepth;
     }
   }
   __syncthreads();
   // 2) normals on the tile plus an R halo
+  if constexpr (K == 2) {
+    for (int i = tid; i < NH * NW; i += NT) {
+      const int lr = i / NW + R, lc = i % NW + R;
+      float4 nv[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int q0 = lr * RW + lc;
+        nv[k] = s_act[q0][k] ? normal_pair<R>(st, s_tm, RW, lr, lc, s_t[q0][k]) : make_float4(0.f, 0.f, 1.f, 0.f);
+      }
+      s_nx[i] = make_float2(nv[0].x, nv[1].x);
+      s_ny[i] = make_float2(nv[0].y, nv[1].y);
+      s_nz[i] = make_float2(nv[0].z, nv[1].z);
+    }
+  } else {
   for (int i = tid; i < NH * NW; i += NT) {
     const int lr = i / NW + R, lc = i % NW + R;  // region coordinates
 #pragma unroll
@@ -423,6 +559,7 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
       s_n[i][k] = nv;
     }
   }
+  }
   __syncthreads();
   // 3) sphere projection, smoothing and pruning on the tile
   if (tid >= kTW * kTH) return;
@@ -433,6 +570,20 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
   const int q0 = lr * RW + lc;
   float tout[K], aout[K];
   bool aact[K];
+  if constexpr (K == 2) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float tq = s_t[q0][k];
+      tout[k] = tq;
+      aout[k] = 0.f;
+      aact[k] = false;
+      if (!s_act[q0][k]) continue;
+      float an;
+      tout[k] = project_pair<R>(st, s_tm, s_a, s_nx, s_ny, s_nz, RW, NW, lr, lc, tq, s_a[q0][k], &an);
+      aact[k] = an >= st.prune_alpha;
+      aout[k] = aact[k] ? an : 0.f;
+    }
+  } else {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float tq = s_t[q0][k];
@@ -472,6 +623,7 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
     const float an = (1.f - st.lambda) * s_a[q0][k] + st.lambda * (Swa / Sw);
     aact[k] = an >= st.prune_alpha;
     aout[k] = aact[k] ? an : 0.f;
+  }
   }
   float sum = 0.f;
 #pragma unroll
@@ -574,7 +726,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, uint3
 // iterations the state goes through global memory (ping-pong buffers) and a
 // grid barrier.
 template <int K, int R>
-__global__ void __launch_bounds__(iter_threads<R>()) k_iter_persistent(
+__global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
     float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x,

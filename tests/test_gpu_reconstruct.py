@@ -276,7 +276,8 @@ def test_invalid_params_rejected(ctx):
     a = torch.zeros(4, 2, device="cuda")
     act = torch.zeros(4, 2, dtype=torch.uint8, device="cuda")
     a0 = torch.zeros(4, device="cuda")
-    for kw in (dict(k_max=3), dict(radius=0), dict(radius=4), dict(apss_h=0.0), dict(smooth_lambda=1.5)):
+    for kw in (dict(k_max=3), dict(radius=0), dict(radius=4), dict(apss_h=0.0), dict(smooth_lambda=1.5),
+               dict(d_max=2e6), dict(depth_scale=2e3)):
         prm = B.make_params(**kw)
         with pytest.raises(B.SRT3DError) as ei:
             B.srt3d_reconstruct(ctx, z, n, 2, 2, T, m, h, prm, d, a, act, a0)
