@@ -441,189 +441,235 @@ __host__ __device__ constexpr int iter_threads() {
   return (((kTW + 4 * R) * (kTH + 4 * R) + 31) / 32) * 32;
 }
 
+// Shared memory of one tile: the post-gradient state of the region (tile +
+// 2R halo) with a masked depth copy, and the normals of the tile + R halo
+// (for K = 2 held as component pairs of the two points in the same storage).
 template <int K, int R>
-__device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uint32_t tile_y,
-                                          const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
-                                          uint32_t m, const float2* __restrict__ hh_g,
-                                          const float* __restrict__ misc, const float* __restrict__ depth_in,
-                                          const float* __restrict__ alpha_in, const uint8_t* __restrict__ active_in,
-                                          float* __restrict__ depth, float* __restrict__ alpha,
-                                          uint8_t* __restrict__ active, float* __restrict__ alpha0,
-                                          const float2* s_z = nullptr, const uint32_t* s_nn = nullptr) {
-  constexpr int H = 2 * R;
-  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
-  constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
-  __shared__ float s_t[RH * RW][K];
-  __shared__ __align__(8) float s_a[RH * RW][K];
-  __shared__ uint8_t s_act[RH * RW][K];
-  __shared__ __align__(8) float s_tm[RH * RW][K];  // depth, or kMaskedDepth for an inactive point
-  __shared__ float4 s_n[NH * NW][K];
-  __shared__ float2 s_hh[kMaxM];
-  // K = 2: normals as component pairs (point 0, point 1) in the same storage
-  float2* s_nx = reinterpret_cast<float2*>(&s_n[0][0]);
-  float2* s_ny = s_nx + NH * NW;
-  float2* s_nz = s_ny + NH * NW;
-  const int tid = threadIdx.x;
-  if (tid < int(m)) s_hh[tid] = hh_g[tid];
-  __syncthreads();
-  const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
-  const float nmax = misc[MISC_NMAX];
-  const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
-  // 1) gradient step on the region (pixels outside the array are inactive)
-  constexpr int NT = iter_threads<R>();
-  for (int i = tid; i < RH * RW; i += NT) {
-    const int rr = r0 - H + i / RW, cc = c0 - H + i % RW;
-    float t[K], a[K];
-    bool act[K];
-    if (rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols)) {
+struct TileSmem {
+  static constexpr int H = 2 * R;
+  static constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
+  static constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
+  static constexpr int HALO = RH * RW - kTW * kTH;          // region pixels outside the tile
+  alignas(16) float4 n[NH * NW][K];
+  alignas(8) float t[RH * RW][K];
+  alignas(8) float a[RH * RW][K];
+  alignas(8) float tm[RH * RW][K];  // depth, or kMaskedDepth for an inactive point
+  uint8_t act[RH * RW][K];
+  float2 hh[kMaxM];
+  __device__ float2* nx() { return reinterpret_cast<float2*>(&n[0][0]); }
+  __device__ float2* ny() { return nx() + NH * NW; }
+  __device__ float2* nz() { return ny() + NH * NW; }
+};
+
+// Region index of the j-th halo pixel (top band, side columns, bottom band).
+template <int R>
+__device__ __forceinline__ int halo_index(int j) {
+  constexpr int H = 2 * R, RW = kTW + 2 * H;
+  if (j < H * RW) return j;
+  j -= H * RW;
+  if (j < kTH * 2 * H) {
+    const int c = j % (2 * H);
+    return (H + j / (2 * H)) * RW + (c < H ? c : c + kTW);
+  }
+  return (H + kTH) * RW + (j - kTH * 2 * H);
+}
+
+// The state (t, a, act) of pixel p. L2-coherent loads: inside the
+// persistent kernel the buffers are rewritten by other CTAs.
+template <int K>
+__device__ __forceinline__ void load_state(const float* depth, const float* alpha, const uint8_t* active, size_t p,
+                                           float (&t)[K], float (&a)[K], bool (&act)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    t[k] = __ldcg(depth + p * K + k);
+    a[k] = __ldcg(alpha + p * K + k);
+    act[k] = __ldcg(active + p * K + k) != 0;
+  }
+}
+
+// Gradient step of region pixel i (at array row rr, column cc; `in` = inside
+// the array, else inactive) from the state (t, a, act); the post-step state
+// goes to shared memory. The pixel's sketch comes from s_z / s_nn when given.
+template <int K, int R>
+__device__ __forceinline__ void grad_to_smem(TileSmem<K, R>& sm, const Stencil& st, int i, int rr, int cc, bool in,
+                                             float (&t)[K], float (&a)[K], bool (&act)[K],
+                                             const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
+                                             uint32_t m, float eta_t, float eta_a, const float2* s_z,
+                                             const uint32_t* s_nn) {
+  if (in) {
+    if (s_z)
+      grad_pixel<K>(s_z + size_t(i) * m, s_nn[i], T, m, sm.hh, eta_t, eta_a, t, a, act);
+    else {
       const size_t p = size_t(rr) * st.cols + size_t(cc);
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        t[k] = depth_in[p * K + k];
-        a[k] = alpha_in[p * K + k];
-        act[k] = active_in[p * K + k] != 0;
-      }
-      if (s_z)  // the region's sketches, kept in shared memory across iterations
-        grad_pixel<K>(s_z + size_t(i) * m, s_nn[i], T, m, s_hh, eta_t, eta_a, t, a, act);
-      else
-        grad_pixel<K>(z + p * m, n[p], T, m, s_hh, eta_t, eta_a, t, a, act);
-    } else {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        t[k] = 0.f;
-        a[k] = 0.f;
-        act[k] = false;
-      }
+      grad_pixel<K>(z + p * m, n[p], T, m, sm.hh, eta_t, eta_a, t, a, act);
     }
+  } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      s_t[i][k] = t[k];
-      s_a[i][k] = a[k];
-      s_act[i][k] = act[k] ? 1 : 0;
-      s_tm[i][k] = act[k] ? t[k] : kMaskedDepth;
+      t[k] = 0.f;
+      a[k] = 0.f;
+      act[k] = false;
     }
   }
-  __syncthreads();
-  // 2) normals on the tile plus an R halo
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    sm.t[i][k] = t[k];
+    sm.a[i][k] = a[k];
+    sm.act[i][k] = act[k] ? 1 : 0;
+    sm.tm[i][k] = act[k] ? t[k] : kMaskedDepth;
+  }
+}
+
+// Stage 1 for region pixel i, its state read from global memory.
+template <int K, int R>
+__device__ __forceinline__ void stage1_pixel(TileSmem<K, R>& sm, const Stencil& st, int i, int r0, int c0,
+                                             const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
+                                             uint32_t m, float eta_t, float eta_a, const float* depth_in,
+                                             const float* alpha_in, const uint8_t* active_in, const float2* s_z,
+                                             const uint32_t* s_nn) {
+  constexpr int H = TileSmem<K, R>::H, RW = TileSmem<K, R>::RW;
+  const int rr = r0 - H + i / RW, cc = c0 - H + i % RW;
+  const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
+  float t[K], a[K];
+  bool act[K];
+  if (in) load_state<K>(depth_in, alpha_in, active_in, size_t(rr) * st.cols + size_t(cc), t, a, act);
+  grad_to_smem<K, R>(sm, st, i, rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z, s_nn);
+}
+
+// Stage 2: normals of the tile plus an R halo.
+template <int K, int R>
+__device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st) {
+  constexpr int RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW, NH = TileSmem<K, R>::NH;
+  constexpr int NT = iter_threads<R>();
+  const int tid = threadIdx.x;
   if constexpr (K == 2) {
+    float2* s_nx = sm.nx();
+    float2* s_ny = sm.ny();
+    float2* s_nz = sm.nz();
     for (int i = tid; i < NH * NW; i += NT) {
       const int lr = i / NW + R, lc = i % NW + R;
+      const int q0 = lr * RW + lc;
       float4 nv[2];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int q0 = lr * RW + lc;
-        nv[k] = s_act[q0][k] ? normal_pair<R>(st, s_tm, RW, lr, lc, s_t[q0][k]) : make_float4(0.f, 0.f, 1.f, 0.f);
-      }
+      for (int k = 0; k < 2; ++k)
+        nv[k] = sm.act[q0][k] ? normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[q0][k]) : make_float4(0.f, 0.f, 1.f, 0.f);
       s_nx[i] = make_float2(nv[0].x, nv[1].x);
       s_ny[i] = make_float2(nv[0].y, nv[1].y);
       s_nz[i] = make_float2(nv[0].z, nv[1].z);
     }
   } else {
-  for (int i = tid; i < NH * NW; i += NT) {
-    const int lr = i / NW + R, lc = i % NW + R;  // region coordinates
+    for (int i = tid; i < NH * NW; i += NT) {
+      const int lr = i / NW + R, lc = i % NW + R;  // region coordinates
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      float4 nv = make_float4(0.f, 0.f, 1.f, 0.f);
-      const int q0 = lr * RW + lc;
-      if (s_act[q0][k]) {
-        const float tq = s_t[q0][k];
-        float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
-        int cnt = 0;
-        // branch-free: every slot is loaded and weighted (0 for non-neighbours),
-        // which leaves the sums exactly as if the slot were skipped
+      for (int k = 0; k < K; ++k) {
+        float4 nv = make_float4(0.f, 0.f, 1.f, 0.f);
+        const int q0 = lr * RW + lc;
+        if (sm.act[q0][k]) {
+          const float tq = sm.t[q0][k];
+          float Sw = 0, Sx = 0, Sy = 0, Sz = 0, Sxx = 0, Sxy = 0, Syy = 0, Sxz = 0, Syz = 0;
+          int cnt = 0;
+          // branch-free: every slot is loaded and weighted (0 for non-neighbours),
+          // which leaves the sums exactly as if the slot were skipped
 #pragma unroll
-        for (int dr = -R; dr <= R; ++dr)
+          for (int dr = -R; dr <= R; ++dr)
 #pragma unroll
-          for (int dc = -R; dc <= R; ++dc) {
-            const int q = (lr + dr) * RW + (lc + dc);
+            for (int dc = -R; dc <= R; ++dc) {
+              const int q = (lr + dr) * RW + (lc + dc);
 #pragma unroll
-            for (int k2 = 0; k2 < K; ++k2) {
-              const float fx = float(dc), fy = float(dr);
-              float dz;
-              bool ok;
-              const float w = slot_weight(st, fx, fy, s_t[q][k2] - tq, s_act[q][k2] != 0, dz, ok);
-              cnt += ok ? 1 : 0;
-              Sw += w;
-              Sx += w * fx;
-              Sy += w * fy;
-              Sz += w * dz;
-              Sxx += w * fx * fx;
-              Sxy += w * fx * fy;
-              Syy += w * fy * fy;
-              Sxz += w * fx * dz;
-              Syz += w * fy * dz;
+              for (int k2 = 0; k2 < K; ++k2) {
+                const float fx = float(dc), fy = float(dr);
+                float dz;
+                bool ok;
+                const float w = slot_weight(st, fx, fy, sm.t[q][k2] - tq, sm.act[q][k2] != 0, dz, ok);
+                cnt += ok ? 1 : 0;
+                Sw += w;
+                Sx += w * fx;
+                Sy += w * fy;
+                Sz += w * dz;
+                Sxx += w * fx * fx;
+                Sxy += w * fx * fy;
+                Syy += w * fy * fy;
+                Sxz += w * fx * dz;
+                Syz += w * fy * dz;
+              }
             }
-          }
-        nv = plane_normal(cnt, Sw, Sx, Sy, Sz, Sxx, Sxy, Syy, Sxz, Syz);
+          nv = plane_normal(cnt, Sw, Sx, Sy, Sz, Sxx, Sxy, Syy, Sxz, Syz);
+        }
+        sm.n[i][k] = nv;
       }
-      s_n[i][k] = nv;
     }
   }
-  }
-  __syncthreads();
-  // 3) sphere projection, smoothing and pruning on the tile
-  if (tid >= kTW * kTH) return;
+}
+
+// Stage 3: sphere projection, smoothing and pruning of tile pixel tid (tile
+// origin r0, c0). Returns whether the thread owns an in-array tile pixel; its
+// new state is then in (tout, aout, aact) and written to global memory.
+template <int K, int R>
+__device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, int r0, int c0, float* depth,
+                                       float* alpha, uint8_t* active, float* alpha0, float (&tout)[K],
+                                       float (&aout)[K], bool (&aact)[K]) {
+  constexpr int H = TileSmem<K, R>::H, RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
+  const int tid = threadIdx.x;
+  if (tid >= kTW * kTH) return false;
   const int ty = tid / kTW, tx = tid % kTW;
   const int rr = r0 + ty, cc = c0 + tx;
-  if (rr >= int(st.rows) || cc >= int(st.cols)) return;
+  if (rr >= int(st.rows) || cc >= int(st.cols)) return false;
   const int lr = ty + H, lc = tx + H;
   const int q0 = lr * RW + lc;
-  float tout[K], aout[K];
-  bool aact[K];
   if constexpr (K == 2) {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const float tq = s_t[q0][k];
+      const float tq = sm.t[q0][k];
       tout[k] = tq;
       aout[k] = 0.f;
       aact[k] = false;
-      if (!s_act[q0][k]) continue;
+      if (!sm.act[q0][k]) continue;
       float an;
-      tout[k] = project_pair<R>(st, s_tm, s_a, s_nx, s_ny, s_nz, RW, NW, lr, lc, tq, s_a[q0][k], &an);
+      tout[k] = project_pair<R>(st, sm.tm, sm.a, sm.nx(), sm.ny(), sm.nz(), RW, NW, lr, lc, tq, sm.a[q0][k], &an);
       aact[k] = an >= st.prune_alpha;
       aout[k] = aact[k] ? an : 0.f;
     }
   } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float tq = s_t[q0][k];
-    tout[k] = tq;
-    aout[k] = 0.f;
-    aact[k] = false;
-    if (!s_act[q0][k]) continue;
-    float Sw = 0, Spx = 0, Spy = 0, Spz = 0, Snx = 0, Sny = 0, Snz = 0, Spn = 0, Spp = 0, Swa = 0;
-    int cnt = 0;
+    for (int k = 0; k < K; ++k) {
+      const float tq = sm.t[q0][k];
+      tout[k] = tq;
+      aout[k] = 0.f;
+      aact[k] = false;
+      if (!sm.act[q0][k]) continue;
+      float Sw = 0, Spx = 0, Spy = 0, Spz = 0, Snx = 0, Sny = 0, Snz = 0, Spn = 0, Spp = 0, Swa = 0;
+      int cnt = 0;
 #pragma unroll
-    for (int dr = -R; dr <= R; ++dr)
+      for (int dr = -R; dr <= R; ++dr)
 #pragma unroll
-      for (int dc = -R; dc <= R; ++dc) {
-        const int q = (lr + dr) * RW + (lc + dc);
-        const int qn = (lr + dr - R) * NW + (lc + dc - R);
+        for (int dc = -R; dc <= R; ++dc) {
+          const int q = (lr + dr) * RW + (lc + dc);
+          const int qn = (lr + dr - R) * NW + (lc + dc - R);
 #pragma unroll
-        for (int k2 = 0; k2 < K; ++k2) {
-          const float fx = float(dc), fy = float(dr);
-          float dz;
-          bool ok;
-          const float w = slot_weight(st, fx, fy, s_t[q][k2] - tq, s_act[q][k2] != 0, dz, ok);
-          cnt += ok ? 1 : 0;
-          const float4 nv = s_n[qn][k2];
-          Sw += w;
-          Spx += w * fx;
-          Spy += w * fy;
-          Spz += w * dz;
-          Snx += w * nv.x;
-          Sny += w * nv.y;
-          Snz += w * nv.z;
-          Spn += w * (fx * nv.x + fy * nv.y + dz * nv.z);
-          Spp += w * (fx * fx + fy * fy + dz * dz);
-          Swa += w * s_a[q][k2];
+          for (int k2 = 0; k2 < K; ++k2) {
+            const float fx = float(dc), fy = float(dr);
+            float dz;
+            bool ok;
+            const float w = slot_weight(st, fx, fy, sm.t[q][k2] - tq, sm.act[q][k2] != 0, dz, ok);
+            cnt += ok ? 1 : 0;
+            const float4 nv = sm.n[qn][k2];
+            Sw += w;
+            Spx += w * fx;
+            Spy += w * fy;
+            Spz += w * dz;
+            Snx += w * nv.x;
+            Sny += w * nv.y;
+            Snz += w * nv.z;
+            Spn += w * (fx * nv.x + fy * nv.y + dz * nv.z);
+            Spp += w * (fx * fx + fy * fy + dz * dz);
+            Swa += w * sm.a[q][k2];
+          }
         }
-      }
-    tout[k] = sphere_depth(st, tq, cnt, Sw, Spx, Spy, Spz, Snx, Sny, Snz, Spn, Spp);
-    const float an = (1.f - st.lambda) * s_a[q0][k] + st.lambda * (Swa / Sw);
-    aact[k] = an >= st.prune_alpha;
-    aout[k] = aact[k] ? an : 0.f;
-  }
+      tout[k] = sphere_depth(st, tq, cnt, Sw, Spx, Spy, Spz, Snx, Sny, Snz, Spn, Spp);
+      const float an = (1.f - st.lambda) * sm.a[q0][k] + st.lambda * (Swa / Sw);
+      aact[k] = an >= st.prune_alpha;
+      aout[k] = aact[k] ? an : 0.f;
+    }
   }
   float sum = 0.f;
 #pragma unroll
@@ -643,6 +689,37 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
     active[p * K + k] = aact[k] ? 1 : 0;
   }
   alpha0[p] = 1.f - sum;
+  return true;
+}
+
+template <int K, int R>
+__device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uint32_t tile_y,
+                                          const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
+                                          uint32_t m, const float2* __restrict__ hh_g,
+                                          const float* __restrict__ misc, const float* depth_in,
+                                          const float* alpha_in, const uint8_t* active_in, float* depth,
+                                          float* alpha, uint8_t* active, float* alpha0) {
+  __shared__ TileSmem<K, R> sm;
+  constexpr int NT = iter_threads<R>();
+  constexpr int RW = TileSmem<K, R>::RW, RH = TileSmem<K, R>::RH;
+  const int tid = threadIdx.x;
+  if (tid < int(m)) sm.hh[tid] = hh_g[tid];
+  __syncthreads();
+  const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
+  const float nmax = misc[MISC_NMAX];
+  const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
+  // 1) gradient step on the region (pixels outside the array are inactive)
+  for (int i = tid; i < RH * RW; i += NT)
+    stage1_pixel<K, R>(sm, st, i, r0, c0, z, n, T, m, eta_t, eta_a, depth_in, alpha_in, active_in, nullptr,
+                       nullptr);
+  __syncthreads();
+  // 2) normals on the tile plus an R halo
+  stage2<K, R>(sm, st);
+  __syncthreads();
+  // 3) sphere projection, smoothing and pruning on the tile
+  float tout[K], aout[K];
+  bool aact[K];
+  stage3<K, R>(sm, st, r0, c0, depth, alpha, active, alpha0, tout, aout, aact);
 }
 
 // The state is read from (depth_in, alpha_in, active_in) and written to
@@ -690,30 +767,31 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
 
 constexpr long long kGridWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident): arrival
-// counter and generation word in global memory, zeroed by k_prep. The wait is
-// bounded: after kGridWaitCycles the CTA latches FLAG_DEVICE_TIMEOUT, marks
-// itself aborted and returns false.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, uint32_t* flags, int* s_abort) {
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident), split
+// into arrive and wait so that work needing no other CTA's data can run in
+// between. Arrivals increment a monotone counter in global memory (zeroed by
+// k_prep); the e-th barrier (e = 0, 1, ...) is complete when the counter
+// reaches (e + 1) x nblocks. The wait is bounded: after kGridWaitCycles the
+// CTA latches FLAG_DEVICE_TIMEOUT, marks itself aborted and returns false.
+__device__ __forceinline__ void grid_arrive(unsigned* bar) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
     __threadfence();
-    if (atomicAdd(bar, 1u) == nblocks - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > kGridWaitCycles) {
-          *s_abort = 1;
-          atomicOr(flags, FLAG_DEVICE_TIMEOUT);
-          break;
-        }
-        __nanosleep(64);
+    atomicAdd(bar, 1u);
+  }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32_t* flags, int* s_abort) {
+  if (threadIdx.x == 0) {
+    volatile unsigned* cnt = bar;
+    const long long t0 = clock64();
+    while (*cnt < target) {
+      if (clock64() - t0 > kGridWaitCycles) {
+        *s_abort = 1;
+        atomicOr(flags, FLAG_DEVICE_TIMEOUT);
+        break;
       }
+      __nanosleep(32);
     }
     __threadfence();
   }
@@ -724,44 +802,76 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, uint3
 // All iterations in one cooperative launch, one CTA per tile: the tile's
 // region of sketches and counts is loaded into shared memory once; between
 // iterations the state goes through global memory (ping-pong buffers) and a
-// grid barrier.
+// grid barrier. The gradient step is pixelwise, so a CTA computes the next
+// iteration's step for its own tile from the state it just produced between
+// arriving at the barrier and waiting on it; after the wait it only steps the
+// halo pixels, whose state its neighbours wrote.
 template <int K, int R>
 __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
     float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x,
     uint32_t* __restrict__ flags) {
-  constexpr int H = 2 * R;
-  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
+  using S = TileSmem<K, R>;
+  constexpr int H = S::H, RW = S::RW, RH = S::RH;
   constexpr int NT = iter_threads<R>();
+  __shared__ S sm;
+  __shared__ int s_abort;
   extern __shared__ float2 s_z[];  // [RH * RW][m] sketches, then [RH * RW] counts
   uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(RH) * RW * m);
-  __shared__ int s_abort;
+  const int tid = threadIdx.x;
   const uint32_t tile_x = blockIdx.x % tiles_x, tile_y = blockIdx.x / tiles_x;
-  const int r0 = int(tile_y) * kTH - H, c0 = int(tile_x) * kTW - H;
-  for (uint32_t i = threadIdx.x; i < uint32_t(RH * RW) * m; i += NT) {
+  const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
+  for (uint32_t i = tid; i < uint32_t(RH * RW) * m; i += NT) {
     const uint32_t q = i / m, l = i - q * m;
-    const int rr = r0 + int(q) / RW, cc = c0 + int(q) % RW;
+    const int rr = r0 - H + int(q) / RW, cc = c0 - H + int(q) % RW;
     const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
     s_z[i] = in ? z[(size_t(rr) * st.cols + size_t(cc)) * m + l] : make_float2(0.f, 0.f);
   }
-  for (uint32_t q = threadIdx.x; q < uint32_t(RH * RW); q += NT) {
-    const int rr = r0 + int(q) / RW, cc = c0 + int(q) % RW;
+  for (uint32_t q = tid; q < uint32_t(RH * RW); q += NT) {
+    const int rr = r0 - H + int(q) / RW, cc = c0 - H + int(q) % RW;
     const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
     s_nn[q] = in ? n[size_t(rr) * st.cols + size_t(cc)] : 0u;
   }
-  if (threadIdx.x == 0) s_abort = 0;
+  if (tid < int(m)) sm.hh[tid] = hh_g[tid];
+  if (tid == 0) s_abort = 0;
   __syncthreads();
+  const float nmax = misc[MISC_NMAX];
+  const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   unsigned* bar = reinterpret_cast<unsigned*>(misc) + MISC_BAR;
+  float tout[K], aout[K];
+  bool aact[K];
   for (uint32_t it = 0; it < iters; ++it) {
     const bool from_alt = ((iters - it) & 1u) != 0;  // the last iteration writes the caller's buffers
-    if (from_alt)
-      iter_tile<K, R>(st, tile_x, tile_y, z, n, T, m, hh_g, misc, alt_d, alt_a, alt_c, depth, alpha, active, alpha0,
-                      s_z, s_nn);
-    else
-      iter_tile<K, R>(st, tile_x, tile_y, z, n, T, m, hh_g, misc, depth, alpha, active, alt_d, alt_a, alt_c, alpha0,
-                      s_z, s_nn);
-    if (it + 1 < iters && !grid_sync(bar, gridDim.x, flags, &s_abort)) break;
+    const float* d_in = from_alt ? alt_d : depth;
+    const float* a_in = from_alt ? alt_a : alpha;
+    const uint8_t* c_in = from_alt ? alt_c : active;
+    float* d_out = from_alt ? depth : alt_d;
+    float* a_out = from_alt ? alpha : alt_a;
+    uint8_t* c_out = from_alt ? active : alt_c;
+    // 1) gradient step: the whole region at the first iteration, else the
+    // halo (the tile's own pixels were stepped before the last barrier wait)
+    if (it == 0) {
+      for (int i = tid; i < RH * RW; i += NT)
+        stage1_pixel<K, R>(sm, st, i, r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z, s_nn);
+    } else {
+      for (int j = tid; j < S::HALO; j += NT)
+        stage1_pixel<K, R>(sm, st, halo_index<R>(j), r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z,
+                           s_nn);
+    }
+    __syncthreads();
+    // 2) normals, 3) projection, smoothing and pruning
+    stage2<K, R>(sm, st);
+    __syncthreads();
+    const bool own = stage3<K, R>(sm, st, r0, c0, d_out, a_out, c_out, alpha0, tout, aout, aact);
+    if (it + 1 == iters) break;
+    grid_arrive(bar);
+    if (tid < kTW * kTH) {
+      const int ty = tid / kTW, tx = tid % kTW;
+      grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), r0 + ty, c0 + tx, own, tout, aout, aact, z, n, T, m,
+                         eta_t, eta_a, s_z, s_nn);
+    }
+    if (!grid_wait(bar, (it + 1u) * gridDim.x, flags, &s_abort)) break;
   }
 }
 
