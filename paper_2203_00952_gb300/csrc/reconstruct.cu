@@ -161,10 +161,71 @@ __global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restric
 
 // Sketched gradient step (Jacobi) of one pixel's K points: reads the state
 // (t, a, act), returns the post-step (t, a); inactive points keep t, get a = 0.
+// The gradient step of a pixel's two points (K = 2) with the phases and
+// residual products of both points in packed FP32 pairs: per harmonic, q_k =
+// hhat_l e^{i w_l t_k}, psi = sum_k a_k q_k, r = z_l - psi, the alpha gradient
+// sums r . q_k, the depth gradient sums w_l Im(conj(q_k) r) (times a_k at the
+// end), and e^{i w_l t_k} advances by one complex rotation.
+__device__ __forceinline__ void grad_pixel_pair(const float2* __restrict__ zp, uint32_t cnt, uint32_t T, uint32_t m,
+                                                const float2* s_hh, float eta_t, float eta_a, float (&t)[2],
+                                                float (&a)[2], const bool (&act)[2]) {
+  const float Tf = float(T);
+  float s0, c0, s1, c1;
+  sincospif(2.f * t[0] / Tf, &s0, &c0);
+  sincospif(2.f * t[1] / Tf, &s1, &c1);
+  const float2 e1x = make_float2(c0, c1), e1y = make_float2(s0, s1), ne1y = make_float2(-s0, -s1);
+  float2 Ex = e1x, Ey = e1y;
+  const float aa0 = act[0] ? a[0] : 0.f, aa1 = act[1] ? a[1] : 0.f;
+  float2 ga = make_float2(0.f, 0.f), gt = ga;
+  const float wstep = 6.283185307179586f / Tf;
+#pragma unroll 4
+  for (uint32_t l = 0; l < m; ++l) {
+    const float2 hv = s_hh[l];
+    const float2 zl = zp[l];
+    const float2 hx = make_float2(hv.x, hv.x), hy = make_float2(hv.y, hv.y), nhy = make_float2(-hv.y, -hv.y);
+    const float2 qx = ffma2(hx, Ex, fmul2(nhy, Ey));
+    const float2 qy = ffma2(hx, Ey, fmul2(hy, Ex));
+    const float rx = zl.x - fmaf(aa1, qx.y, aa0 * qx.x);
+    const float ry = zl.y - fmaf(aa1, qy.y, aa0 * qy.x);
+    ga = ffma2(make_float2(ry, ry), qy, ffma2(make_float2(rx, rx), qx, ga));
+    const float w = wstep * float(l + 1);
+    const float2 cr = ffma2(make_float2(ry, ry), qx, fmul2(make_float2(-rx, -rx), qy));
+    gt = ffma2(make_float2(w, w), cr, gt);
+    const float2 nEx = ffma2(Ex, e1x, fmul2(Ey, ne1y));
+    Ey = ffma2(Ex, e1y, fmul2(Ey, e1x));
+    Ex = nEx;
+  }
+  const float nn = -2.f * float(cnt);
+  const float gtk[2] = {a[0] * gt.x, a[1] * gt.y}, gak[2] = {ga.x, ga.y};
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (act[k]) {
+      float x = t[k] - eta_t * (nn * gtk[k]);
+      x -= floorf(x / Tf) * Tf;
+      if (x >= Tf) x -= Tf;
+      if (x < 0.f) x += Tf;
+      t[k] = x;
+      a[k] = fmaxf(a[k] - eta_a * (nn * gak[k]), 0.f);
+    } else {
+      a[k] = 0.f;
+    }
+    sum += a[k];
+  }
+  if (sum > 1.f) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) a[k] = a[k] / sum;
+  }
+}
+
 template <int K>
 __device__ __forceinline__ void grad_pixel(const float2* __restrict__ zp, uint32_t cnt, uint32_t T, uint32_t m,
                                            const float2* s_hh, float eta_t, float eta_a, float (&t)[K],
                                            float (&a)[K], const bool (&act)[K]) {
+  if constexpr (K == 2) {
+    grad_pixel_pair(zp, cnt, T, m, s_hh, eta_t, eta_a, t, a, act);
+    return;
+  }
   const float Tf = float(T);
   float2 e1[K], E[K];
 #pragma unroll
