@@ -510,7 +510,6 @@ struct TileSmem {
   static constexpr int H = 2 * R;
   static constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;  // post-gradient region
   static constexpr int NW = kTW + 2 * R, NH = kTH + 2 * R;  // normals region
-  static constexpr int HALO = RH * RW - kTW * kTH;          // region pixels outside the tile
   alignas(16) float4 n[NH * NW][K];
   alignas(8) float t[RH * RW][K];
   alignas(8) float a[RH * RW][K];
@@ -522,17 +521,18 @@ struct TileSmem {
   __device__ float2* nz() { return ny() + NH * NW; }
 };
 
-// Region index of the j-th halo pixel (top band, side columns, bottom band).
+// Region index of the j-th halo pixel of a tile th rows high (top band, side
+// columns, bottom band).
 template <int R>
-__device__ __forceinline__ int halo_index(int j) {
+__device__ __forceinline__ int halo_index(int j, int th) {
   constexpr int H = 2 * R, RW = kTW + 2 * H;
   if (j < H * RW) return j;
   j -= H * RW;
-  if (j < kTH * 2 * H) {
+  if (j < th * 2 * H) {
     const int c = j % (2 * H);
     return (H + j / (2 * H)) * RW + (c < H ? c : c + kTW);
   }
-  return (H + kTH) * RW + (j - kTH * 2 * H);
+  return (H + th) * RW + (j - th * 2 * H);
 }
 
 // The state (t, a, act) of pixel p. L2-coherent loads: inside the
@@ -597,10 +597,11 @@ __device__ __forceinline__ void stage1_pixel(TileSmem<K, R>& sm, const Stencil& 
   grad_to_smem<K, R>(sm, st, i, rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z, s_nn);
 }
 
-// Stage 2: normals of the tile plus an R halo.
+// Stage 2: normals of the tile (th rows) plus an R halo.
 template <int K, int R>
-__device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st) {
-  constexpr int RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW, NH = TileSmem<K, R>::NH;
+__device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, int th) {
+  constexpr int RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
+  const int NH = th + 2 * R;
   constexpr int NT = iter_threads<R>();
   const int tid = threadIdx.x;
   if constexpr (K == 2) {
@@ -663,15 +664,16 @@ __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st) {
 }
 
 // Stage 3: sphere projection, smoothing and pruning of tile pixel tid (tile
-// origin r0, c0). Returns whether the thread owns an in-array tile pixel; its
-// new state is then in (tout, aout, aact) and written to global memory.
+// origin r0, c0, th rows). Returns whether the thread owns an in-array tile
+// pixel; its new state is then in (tout, aout, aact) and written to global
+// memory.
 template <int K, int R>
-__device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, int r0, int c0, float* depth,
+__device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, int r0, int c0, int th, float* depth,
                                        float* alpha, uint8_t* active, float* alpha0, float (&tout)[K],
                                        float (&aout)[K], bool (&aact)[K]) {
   constexpr int H = TileSmem<K, R>::H, RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
   const int tid = threadIdx.x;
-  if (tid >= kTW * kTH) return false;
+  if (tid >= kTW * th) return false;
   const int ty = tid / kTW, tx = tid % kTW;
   const int rr = r0 + ty, cc = c0 + tx;
   if (rr >= int(st.rows) || cc >= int(st.cols)) return false;
@@ -775,12 +777,12 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
                        nullptr);
   __syncthreads();
   // 2) normals on the tile plus an R halo
-  stage2<K, R>(sm, st);
+  stage2<K, R>(sm, st, kTH);
   __syncthreads();
   // 3) sphere projection, smoothing and pruning on the tile
   float tout[K], aout[K];
   bool aact[K];
-  stage3<K, R>(sm, st, r0, c0, depth, alpha, active, alpha0, tout, aout, aact);
+  stage3<K, R>(sm, st, r0, c0, kTH, depth, alpha, active, alpha0, tout, aout, aact);
 }
 
 // The state is read from (depth_in, alpha_in, active_in) and written to
@@ -866,23 +868,25 @@ __device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32
 // grid barrier. The gradient step is pixelwise, so a CTA computes the next
 // iteration's step for its own tile from the state it just produced between
 // arriving at the barrier and waiting on it; after the wait it only steps the
-// halo pixels, whose state its neighbours wrote.
+// halo pixels, whose state its neighbours wrote. Tiles are kTW x th (th <=
+// kTH, chosen by the launcher to balance the tiles over the SMs).
 template <int K, int R>
 __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
-    float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x,
+    float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x, uint32_t th_u,
     uint32_t* __restrict__ flags) {
   using S = TileSmem<K, R>;
-  constexpr int H = S::H, RW = S::RW, RH = S::RH;
+  constexpr int H = S::H, RW = S::RW;
+  const int th = int(th_u), RH = th + 2 * H, halo = RH * RW - kTW * th;
   constexpr int NT = iter_threads<R>();
   __shared__ S sm;
   __shared__ int s_abort;
   extern __shared__ float2 s_z[];  // [RH * RW][m] sketches, then [RH * RW] counts
-  uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(RH) * RW * m);
+  uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(S::RH) * RW * m);
   const int tid = threadIdx.x;
   const uint32_t tile_x = blockIdx.x % tiles_x, tile_y = blockIdx.x / tiles_x;
-  const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
+  const int r0 = int(tile_y) * th, c0 = int(tile_x) * kTW;
   for (uint32_t i = tid; i < uint32_t(RH * RW) * m; i += NT) {
     const uint32_t q = i / m, l = i - q * m;
     const int rr = r0 - H + int(q) / RW, cc = c0 - H + int(q) % RW;
@@ -916,18 +920,18 @@ __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_pers
       for (int i = tid; i < RH * RW; i += NT)
         stage1_pixel<K, R>(sm, st, i, r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z, s_nn);
     } else {
-      for (int j = tid; j < S::HALO; j += NT)
-        stage1_pixel<K, R>(sm, st, halo_index<R>(j), r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z,
+      for (int j = tid; j < halo; j += NT)
+        stage1_pixel<K, R>(sm, st, halo_index<R>(j, th), r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z,
                            s_nn);
     }
     __syncthreads();
     // 2) normals, 3) projection, smoothing and pruning
-    stage2<K, R>(sm, st);
+    stage2<K, R>(sm, st, th);
     __syncthreads();
-    const bool own = stage3<K, R>(sm, st, r0, c0, d_out, a_out, c_out, alpha0, tout, aout, aact);
+    const bool own = stage3<K, R>(sm, st, r0, c0, th, d_out, a_out, c_out, alpha0, tout, aout, aact);
     if (it + 1 == iters) break;
     grid_arrive(bar);
-    if (tid < kTW * kTH) {
+    if (tid < kTW * th) {
       const int ty = tid / kTW, tx = tid % kTW;
       grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), r0 + ty, c0 + tx, own, tout, aout, aact, z, n, T, m,
                          eta_t, eta_a, s_z, s_nn);
@@ -971,17 +975,40 @@ __global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint
   alpha0[p] = 1.f - s;
 }
 
+// Tile height for the persistent kernel: the th in [4, kTH] whose tiles all
+// fit on the device at once (bps CTAs per SM) and minimise the work of the
+// busiest SM, ceil(tiles / SMs) x the per-tile work (pixels of the gradient
+// region + normals region + 2 x tile, the projection weighing double). 0 if
+// no th fits.
+template <int R>
+uint32_t persistent_tile_height(uint32_t rows, uint32_t cols, int num_sms, int bps) {
+  constexpr int H = 2 * R;
+  const uint64_t tiles_x = (cols + kTW - 1) / kTW;
+  uint32_t best = 0;
+  uint64_t best_cost = ~uint64_t(0);
+  for (uint32_t th = kTH; th >= 4; --th) {
+    const uint64_t ntiles = tiles_x * ((rows + th - 1) / th);
+    if (ntiles > uint64_t(num_sms) * uint64_t(bps)) continue;
+    const uint64_t per_tile = uint64_t(th + 2 * H) * (kTW + 2 * H) + uint64_t(th + 2 * R) * (kTW + 2 * R) +
+                              2ull * kTW * th;
+    const uint64_t cost = (ntiles + num_sms - 1) / num_sms * per_tile;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = th;
+    }
+  }
+  return best;
+}
+
 // Cooperative launch of k_iter_persistent; SRT3D_EAGAIN when the tiles do
 // not all fit on the device at once (the caller then launches per iteration).
 template <int K, int R>
 srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const float2* z, const uint32_t* n,
                                     uint32_t T, uint32_t m, const Scratch& sc, float* depth, float* alpha,
-                                    uint8_t* active, float* alpha0, uint32_t iters, dim3 tiles,
-                                    cudaStream_t stream) {
+                                    uint8_t* active, float* alpha0, uint32_t iters, cudaStream_t stream) {
   constexpr int H = 2 * R;
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
   const size_t zsmem = size_t(RH) * RW * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
-  const uint32_t ntiles = tiles.x * tiles.y;
   auto fn = k_iter_persistent<K, R>;
   cudaFuncAttributes fa;
   SRT3D_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, fn));
@@ -990,17 +1017,20 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
   int bps = 0;
   SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, iter_threads<R>(), zsmem));
-  if (uint64_t(bps) * uint64_t(ctx->num_sms) < ntiles) return SRT3D_EAGAIN;
+  const uint32_t th = persistent_tile_height<R>(st.rows, st.cols, ctx->num_sms, bps);
+  if (th == 0) return SRT3D_EAGAIN;
+  const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
+  const uint32_t ntiles = tiles_x * ((st.rows + th - 1) / th);
   Stencil stv = st;
   const float2* zz = z;
   const uint32_t* nn = n;
-  uint32_t TT = T, mm = m, it = iters, tx = tiles.x;
+  uint32_t TT = T, mm = m, it = iters, tx = tiles_x, thv = th;
   const float2* hh = sc.hh;
   float* misc = sc.misc;
   float *d = depth, *a = alpha, *a0 = alpha0, *ad = sc.t1, *aa = sc.a1;
   uint8_t *c = active, *ac = sc.act1;
   uint32_t* flags = ctx->d_flags;
-  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &ad, &aa, &ac, &it, &tx, &flags};
+  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &ad, &aa, &ac, &it, &tx, &thv, &flags};
   const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
   SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles), dim3(iter_threads<R>()),
                                                   args, zsmem, stream));
@@ -1064,13 +1094,13 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     srt3d_status pst = SRT3D_EAGAIN;
     if (allow) {
       if (prm.radius == 1)
-        pst = launch_iter_persistent<K, 1>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+        pst = launch_iter_persistent<K, 1>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
                                            stream);
       else if (prm.radius == 2)
-        pst = launch_iter_persistent<K, 2>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+        pst = launch_iter_persistent<K, 2>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
                                            stream);
       else
-        pst = launch_iter_persistent<K, 3>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters, tiles,
+        pst = launch_iter_persistent<K, 3>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
                                            stream);
     }
     if (pst != SRT3D_EAGAIN) return pst;  // launched (or failed)
