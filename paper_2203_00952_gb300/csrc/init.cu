@@ -279,12 +279,14 @@ __device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict_
 
 // One warp per pixel. Dynamic shared memory: the phase table, the coarse
 // table e^{i 2 pi g D / T} (G entries) and one row of G grid scores per warp.
+// Also folds the frame's largest photon count n_max (zeroed by the prep
+// kernel) into misc[MISC_NMAX] for the iterations' step sizes.
 template <int K, int M>
 __global__ void __launch_bounds__(kBlock, 1) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
                                                  uint32_t P, uint32_t T, uint32_t m,
                                                  const float2* __restrict__ table, uint32_t entries,
                                                  int two_level, uint32_t D, const float2* __restrict__ hh_g,
-                                                 const float* __restrict__ misc, float prune_alpha, float min_sep,
+                                                 float* __restrict__ misc, float prune_alpha, float min_sep,
                                                  float* __restrict__ depth, float* __restrict__ alpha,
                                                  uint8_t* __restrict__ active, float* __restrict__ alpha0) {
   extern __shared__ float2 s_tab[];
@@ -301,9 +303,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_init(const float2* __restrict__ z
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t wpb = blockDim.x >> 5;
   const float E2 = misc[MISC_E2];
-  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb)
+  uint32_t nmax = 0u;  // largest photon count seen by this warp
+  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb) {
+    nmax = max(nmax, n[p]);
     init_pixel<K, M>(p, z, n, T, m, s_tab, tl, s_wg, s_grid_all + warp * G, D, G, s_hh, E2, prune_alpha, min_sep,
                      depth, alpha, active, alpha0);
+  }
+  if ((threadIdx.x & 31u) == 0u) atomicMax(reinterpret_cast<unsigned*>(misc) + MISC_NMAX, nmax);
 }
 
 // Batched: items (frame, first pixel, last pixel); the CTA reloads the tables
@@ -336,14 +342,18 @@ __global__ void __launch_bounds__(kBlock, 1) k_init_batch(const BatchFrame* __re
       cur = item.x;
     }
     const float E2 = f.misc[MISC_E2];
-    for (uint32_t p = item.y + warp; p < item.z; p += wpb)
+    uint32_t nmax = 0u;
+    for (uint32_t p = item.y + warp; p < item.z; p += wpb) {
+      nmax = max(nmax, f.n[p]);
       init_pixel<K, M>(p, f.S, f.n, f.T, f.m, s_tab, tl, s_wg, s_grid_all + warp * max_G, f.D, G, s_hh, E2,
                        prune_alpha, min_sep, f.depth, f.alpha, f.active, f.alpha0);
+    }
+    if ((threadIdx.x & 31u) == 0u) atomicMax(reinterpret_cast<unsigned*>(f.misc) + MISC_NMAX, nmax);
   }
 }
 
 using InitFn = void (*)(const float2*, const uint32_t*, uint32_t, uint32_t, uint32_t, const float2*, uint32_t, int,
-                        uint32_t, const float2*, const float*, float, float, float*, float*, uint8_t*, float*);
+                        uint32_t, const float2*, float*, float, float, float*, float*, uint8_t*, float*);
 using InitBatchFn = void (*)(const BatchFrame*, const uint3*, uint32_t, uint32_t, uint32_t, float, float);
 
 template <int K>
@@ -379,7 +389,7 @@ int init_round_m(uint32_t m) {
 uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m) { return mf_grid_spacing_impl(T, m); }
 
 srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
-                         uint32_t K, const PhaseTable& tab, const float2* hh, const float* misc,
+                         uint32_t K, const PhaseTable& tab, const float2* hh, float* misc,
                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
                          cudaStream_t stream) {
   const int M = init_round_m(m);

@@ -157,9 +157,10 @@ srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames
                                       const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
                                       uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
                                       cudaStream_t stream);
-// Matched-filter initialisation (init.cu): hh = hhat[m], misc = frame scalars.
+// Matched-filter initialisation (init.cu): hh = hhat[m], misc = frame scalars
+// (misc[MISC_NMAX] receives the largest photon count, as an unsigned).
 srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
-                         uint32_t K, const PhaseTable& tab, const float2* hh, const float* misc,
+                         uint32_t K, const PhaseTable& tab, const float2* hh, float* misc,
                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
                          cudaStream_t stream);
 // Batched: every frame of the items has m <= M, M an instantiated count.

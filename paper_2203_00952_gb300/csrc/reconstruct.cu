@@ -67,64 +67,46 @@ __device__ __forceinline__ void load_table(float2* s_tab, const float2* table, u
   __syncthreads();
 }
 
-// One block: hhat (FP32 partial sums per thread, then a tree), H, n_max, and
-// the step-size bases eta_t * n_max, eta_alpha * n_max.
+// One block: hhat (one warp per harmonic), H, and the step-size bases
+// eta_t * n_max, eta_alpha * n_max; n_max itself is left to the init kernels,
+// which read every pixel's count anyway.
+constexpr uint32_t kPrepChunk = 4096;
 __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uint32_t* __restrict__ n, uint32_t P,
                                           uint32_t T, uint32_t m, uint32_t K, const float2* __restrict__ table,
                                           uint32_t entries, int two_level, float2* __restrict__ hh_out,
                                           float* __restrict__ misc, float2* s_tab) {
-  __shared__ float s_red[2][32];
-  __shared__ float s_H;
-  __shared__ uint32_t s_nmax;
+  __shared__ float s_h[kPrepChunk];
   load_table(s_tab, table, entries);
   const bool tl = two_level != 0;
   const float invT = 1.0f / float(T);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) s_nmax = 0u;
-  // H = sum h
-  float hs = 0.f;
-  for (uint32_t tau = threadIdx.x; tau < T; tau += blockDim.x) hs += h[tau];
-  for (int off = 16; off; off >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, off);
-  if (lane == 0) s_red[0][warp] = hs;
-  __syncthreads();
-  if (warp == 0) {
-    float v = lane < nw ? s_red[0][lane] : 0.f;
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) s_H = v;
-  }
-  __syncthreads();
-  for (uint32_t l = 1; l <= m; ++l) {
-    float re = 0.f, im = 0.f;
-    for (uint32_t tau = threadIdx.x; tau < T; tau += blockDim.x) {
-      const float2 e = phase(s_tab, mulmod(l, tau, T, invT), tl);
-      const float hv = h[tau];
-      re = fmaf(hv, e.x, re);
-      im = fmaf(hv, e.y, im);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  // warp l - 1 computes hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau}, with its
+  // own H = sum h (m <= 32 warps), over chunks of h staged in shared memory
+  float hs = 0.f, re = 0.f, im = 0.f;
+  const uint32_t l = warp + 1u;
+  for (uint32_t base = 0; base < T; base += kPrepChunk) {
+    const uint32_t len = min(kPrepChunk, T - base);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_h[i] = h[base + i];
+    __syncthreads();
+    if (warp < m) {
+      for (uint32_t i = lane; i < len; i += 32u) {
+        const float2 e = phase(s_tab, mulmod(l, base + i, T, invT), tl);
+        const float hv = s_h[i];
+        hs += hv;
+        re = fmaf(hv, e.x, re);
+        im = fmaf(hv, e.y, im);
+      }
     }
+  }
+  if (warp < m) {
     for (int off = 16; off; off >>= 1) {
+      hs += __shfl_xor_sync(0xffffffffu, hs, off);
       re += __shfl_xor_sync(0xffffffffu, re, off);
       im += __shfl_xor_sync(0xffffffffu, im, off);
     }
-    __syncthreads();
-    if (lane == 0) {
-      s_red[0][warp] = re;
-      s_red[1][warp] = im;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      float vr = lane < nw ? s_red[0][lane] : 0.f;
-      float vi = lane < nw ? s_red[1][lane] : 0.f;
-      for (int off = 16; off; off >>= 1) {
-        vr += __shfl_xor_sync(0xffffffffu, vr, off);
-        vi += __shfl_xor_sync(0xffffffffu, vi, off);
-      }
-      if (lane == 0) hh_out[l - 1] = make_float2(vr / s_H, vi / s_H);
-    }
+    if (lane == 0) hh_out[l - 1] = make_float2(re / hs, im / hs);
   }
-  uint32_t nm = 0u;
-  for (uint32_t p = threadIdx.x; p < P; p += blockDim.x) nm = max(nm, n[p]);
-  for (int off = 16; off; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
-  if (lane == 0) atomicMax(&s_nmax, nm);
   __syncthreads();
   if (threadIdx.x == 0) {
     float sw = 0.f, sa = 0.f;
@@ -138,7 +120,7 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
     misc[MISC_ETA_T] = 1.f / (2.f * sw);
     misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
     misc[MISC_E2] = sa;
-    misc[MISC_NMAX] = float(max(s_nmax, 1u));
+    reinterpret_cast<unsigned*>(misc)[MISC_NMAX] = 0u;  // n_max: atomicMax by the init kernels
     reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
     reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // grid barrier: generation
   }
@@ -295,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, c
   __syncthreads();
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P) return;
-  const float nmax = misc[MISC_NMAX];
+  const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   float t[K], a[K];
   bool act[K];
 #pragma unroll
@@ -769,7 +751,7 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
   if (tid < int(m)) sm.hh[tid] = hh_g[tid];
   __syncthreads();
   const int r0 = int(tile_y) * kTH, c0 = int(tile_x) * kTW;
-  const float nmax = misc[MISC_NMAX];
+  const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   // 1) gradient step on the region (pixels outside the array are inactive)
   for (int i = tid; i < RH * RW; i += NT)
@@ -901,7 +883,7 @@ __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_pers
   if (tid < int(m)) sm.hh[tid] = hh_g[tid];
   if (tid == 0) s_abort = 0;
   __syncthreads();
-  const float nmax = misc[MISC_NMAX];
+  const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   unsigned* bar = reinterpret_cast<unsigned*>(misc) + MISC_BAR;
   float tout[K], aout[K];
@@ -966,8 +948,11 @@ __global__ void k_copy_state_batch(const BatchFrame* __restrict__ frames, uint32
 
 template <int K>
 __global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint8_t* __restrict__ active,
-                         float* __restrict__ alpha0) {
+                         float* __restrict__ alpha0, const uint32_t* __restrict__ n, float* __restrict__ misc) {
   const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t nm = p < P ? n[p] : 0u;
+  for (int off = 16; off; off >>= 1) nm = max(nm, __shfl_xor_sync(0xffffffffu, nm, off));
+  if ((threadIdx.x & 31u) == 0u) atomicMax(reinterpret_cast<unsigned*>(misc) + MISC_NMAX, nm);
   if (p >= P) return;
   float s = 0.f;
 #pragma unroll
@@ -1060,7 +1045,7 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   } else {
     {
       const ProfMark mk = prof_begin(ctx, KID_ALPHA0, stream);
-      k_alpha0<K><<<(P + kBlock - 1) / kBlock, kBlock, 0, stream>>>(P, alpha, active, alpha0);
+      k_alpha0<K><<<(P + kBlock - 1) / kBlock, kBlock, 0, stream>>>(P, alpha, active, alpha0, n, sc.misc);
       prof_end(ctx, KID_ALPHA0, mk, stream);
     }
     SRT3D_CUDA_TRY(ctx, cudaGetLastError());
