@@ -62,6 +62,48 @@ __device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
   return d;
 }
 
+// A packed FP32 pair held in one 64-bit register (low half = first
+// component), so packed operations need no operand marshalling.
+using pf2 = unsigned long long;
+
+__device__ __forceinline__ pf2 pk(float lo, float hi) {
+  pf2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ float2 upk(pf2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+__device__ __forceinline__ float pk_lo(pf2 v) { return __uint_as_float(static_cast<unsigned>(v)); }
+
+__device__ __forceinline__ pf2 pfma(pf2 a, pf2 b, pf2 c) {
+  pf2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ pf2 padd(pf2 a, pf2 b) {
+  pf2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ pf2 psub(pf2 a, pf2 b) {
+  pf2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ pf2 pmul(pf2 a, pf2 b) {
+  pf2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // (j * x) mod T, exact for j * x < 2^24: the product is exact in float, the
 // float quotient is within 1 of floor(j x / T), and one correction fixes it.
 __device__ __forceinline__ uint32_t mulmod(uint32_t j, uint32_t x, uint32_t T, float invT) {

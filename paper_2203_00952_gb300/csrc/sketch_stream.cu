@@ -19,9 +19,10 @@
 // with restarts (checked exhaustively over x for T from 256 to 8192). For
 // T > 8192 the table is two-level and the harmonics come from complex
 // rotation instead (see add_photon). Each
-// lane keeps m complex FP32 partial sums; the group reduces them with xor
-// shuffles at the end of the pixel. No floating-point atomics: the result for
-// a pixel does not depend on what else runs.
+// lane keeps m complex FP32 partial sums; at the end of the pixel the group
+// reduce-scatters them with xor shuffles (each lane ends with a few totals).
+// No floating-point atomics: the result for a pixel does not depend on what
+// else runs.
 #include <cmath>
 #include <cstdio>
 
@@ -37,49 +38,51 @@ constexpr int kRestartAbove = 10;  // ... when m exceeds this
 constexpr int kResyncTL = 16;      // two-level table: resync of the rotation
 
 // acc[j-1] += s_j e^{i w_j x} for j = 1..M, s_j = -1 when j mod 4 is 2 or 3
-// (the caller flips those signs once per pixel). Direct table: Chebyshev
-// recurrence. Two-level table (T > 8192): its composed e_1 carries ~1.5 ulp,
-// which the recurrence would amplify ~j^2-fold, so there the harmonics come
-// from complex rotation e_j = e_{j-1} e_1 (error growing ~j-fold), resynced
-// from the table every 16 harmonics, and the signs are applied per term.
+// (the caller flips those signs once per pixel); acc holds packed (Re, Im)
+// pairs. Direct table: Chebyshev recurrence. Two-level table (T > 8192): its
+// composed e_1 carries ~1.5 ulp, which the recurrence would amplify ~j^2-fold,
+// so there the harmonics come from complex rotation e_j = e_{j-1} e_1 (error
+// growing ~j-fold), resynced from the table every 16 harmonics, and the signs
+// are applied per term.
 template <int M, bool TL>
-__device__ __forceinline__ void add_photon(float2 (&acc)[M], uint32_t x, const float2* tab, uint32_t T,
-                                           float invT) {
-  const float2 e1 = phase(tab, x, TL);
+__device__ __forceinline__ void add_photon(pf2 (&acc)[M], uint32_t x, const float2* tab, uint32_t T, float invT) {
+  const pf2* ptab = reinterpret_cast<const pf2*>(tab);
   if (TL) {
+    const float2 e1 = phase(tab, x, true);
     float2 e = e1;
-    acc[0] = fadd2(acc[0], e);
+    acc[0] = padd(acc[0], pk(e.x, e.y));
 #pragma unroll
     for (int j = 2; j <= M; ++j) {
       if ((j - 1) % kResyncTL == 0)
         e = phase(tab, mulmod(uint32_t(j), x, T, invT), true);
       else
         e = cmul(e, e1);
-      acc[j - 1] = (j & 2) ? fsub2(acc[j - 1], e) : fadd2(acc[j - 1], e);
+      acc[j - 1] = (j & 2) ? psub(acc[j - 1], pk(e.x, e.y)) : padd(acc[j - 1], pk(e.x, e.y));
     }
     return;
   }
-  const float c2 = e1.x + e1.x;
-  const float2 pc = make_float2(c2, c2), nc = make_float2(-c2, -c2);
-  float2 p = make_float2(1.f, 0.f);  // a_{j-2}
-  float2 q = e1;                     // a_{j-1}
-  acc[0] = fadd2(acc[0], q);
+  const pf2 e1 = ptab[x];
+  const float c2 = pk_lo(e1) + pk_lo(e1);
+  const pf2 pc = pk(c2, c2), nc = pk(-c2, -c2);
+  pf2 p = pk(1.f, 0.f);  // a_{j-2}
+  pf2 q = e1;            // a_{j-1}
+  acc[0] = padd(acc[0], q);
 #pragma unroll
   for (int j = 2; j <= M; ++j) {
-    float2 r;
+    pf2 r;
     if (M > kRestartAbove && (j - 1) % kRestart == 0) {
       // a_{j-1} = e_{j-1}, a_j = e_j from the table (s = + at j - 1 = 0 mod 4 and j)
       const uint32_t k0 = mulmod(uint32_t(j - 1), x, T, invT);
       uint32_t k1 = k0 + x;
       k1 -= (k1 >= T) ? T : 0u;
-      q = phase(tab, k0, false);
-      r = phase(tab, k1, false);
+      q = ptab[k0];
+      r = ptab[k1];
     } else {
-      r = ffma2((j & 1) ? pc : nc, q, p);
+      r = pfma((j & 1) ? pc : nc, q, p);
     }
     p = q;
     q = r;
-    acc[j - 1] = fadd2(acc[j - 1], r);
+    acc[j - 1] = padd(acc[j - 1], r);
   }
 }
 
@@ -94,7 +97,7 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
 // All photons of one pixel for lane gl of its group: the loose stamps one
 // per lane, then whole words. Returns whether a stamp was >= T.
 template <int M, bool TL>
-__device__ __forceinline__ bool pixel_photons(float2 (&acc)[M], const uint4* __restrict__ words,
+__device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const uint4* __restrict__ words,
                                               const uint16_t* __restrict__ half, uint32_t a, uint32_t b,
                                               uint32_t nh, uint32_t nl, uint32_t ts, uint32_t wa, uint32_t wb,
                                               uint32_t T, float invT, uint32_t G, uint32_t gl, const float2* s_tab) {
@@ -127,6 +130,73 @@ __device__ __forceinline__ bool pixel_photons(float2 (&acc)[M], const uint4* __r
   return bad;
 }
 
+// Reduce-scatter over the 2^LG lanes of a group: each step exchanges half of
+// the lane's vector with the partner lane (lane ^ offset) and adds, so after
+// LG steps a lane holds the group totals of entries [base, base + cnt) of the
+// original vector in res[0..cnt) (cnt <= RsOut<L, LG>::n; an odd length is
+// padded with a zero entry, which belongs to no one). One shuffle per kept
+// entry per step instead of one per entry per step.
+template <int L, int LG>
+struct RsOut {
+  static constexpr int n = RsOut<(L + 1) / 2, LG - 1>::n;
+};
+template <int L>
+struct RsOut<L, 0> {
+  static constexpr int n = L;
+};
+
+template <int L, int LG>
+__device__ __forceinline__ void reduce_scatter(const float (&v)[L], uint32_t gl, unsigned gmask, uint32_t& base,
+                                               uint32_t& cnt, float (&res)[RsOut<L, LG>::n]) {
+  if constexpr (LG == 0) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) res[i] = v[i];
+  } else {
+    constexpr int half = (L + 1) / 2;
+    constexpr uint32_t o = 1u << (LG - 1);
+    const bool up = (gl & o) != 0;
+    float nv[half];
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const float lo = v[i], hi = (i + half < L) ? v[i + half] : 0.f;
+      nv[i] = (up ? hi : lo) + __shfl_xor_sync(gmask, up ? lo : hi, o);
+    }
+    if (up) {
+      base += half;
+      cnt = cnt > uint32_t(half) ? cnt - uint32_t(half) : 0u;
+    } else {
+      cnt = min(cnt, uint32_t(half));
+    }
+    reduce_scatter<half, LG - 1>(nv, gl, gmask, base, cnt, res);
+  }
+}
+
+// Group totals of the M packed partial sums, signs s_j undone, stored (or
+// accumulated) into S[p][0..m): each lane stores the entries it holds.
+template <int M, int LG>
+__device__ __forceinline__ void store_sums(const pf2 (&acc)[M], uint32_t gl, unsigned gmask, uint32_t m,
+                                           int accumulate, float* __restrict__ Sp) {
+  float v[2 * M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float2 f = upk(acc[j]);
+    v[2 * j] = f.x;
+    v[2 * j + 1] = f.y;
+  }
+  uint32_t base = 0, cnt = 2 * M;
+  float res[RsOut<2 * M, LG>::n];
+  reduce_scatter<2 * M, LG>(v, gl, gmask, base, cnt, res);
+#pragma unroll
+  for (int i = 0; i < RsOut<2 * M, LG>::n; ++i) {
+    const uint32_t idx = base + uint32_t(i);
+    if (uint32_t(i) < cnt && idx < 2u * m) {
+      float x = ((idx >> 1) + 1u) & 2u ? -res[i] : res[i];
+      if (accumulate) x += Sp[idx];
+      Sp[idx] = x;
+    }
+  }
+}
+
 // One pixel of the stream, processed by a group of G lanes: coalesced 16-byte
 // words from the aligned base, per-lane partial sums, xor-shuffle reduction,
 // store (or accumulate) of S[p][0..m) and n[p].
@@ -142,9 +212,9 @@ __device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, ui
     if (gl == 0) atomicOr(flags, FLAG_OFFSETS);
     s = e = 0;
   }
-  float2 acc[M];
+  pf2 acc[M];
 #pragma unroll
-  for (int j = 0; j < M; ++j) acc[j] = make_float2(0.f, 0.f);
+  for (int j = 0; j < M; ++j) acc[j] = 0ull;  // (+0, +0)
   // positions relative to the aligned base; whole words [wa, wb), loose
   // stamps [a, he) and [ts, b)
   const uint32_t a = s + shift, b = e + shift;
@@ -155,24 +225,12 @@ __device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, ui
   const bool bad = tl ? pixel_photons<M, true>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab)
                       : pixel_photons<M, false>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab);
   if (bad) atomicOr(flags, FLAG_STAMP_RANGE);
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    for (uint32_t off = G >> 1; off > 0; off >>= 1)
-      acc[j] = fadd2(acc[j], make_float2(__shfl_xor_sync(gmask, acc[j].x, off), __shfl_xor_sync(gmask, acc[j].y, off)));
-    if ((j + 1) & 2) acc[j] = make_float2(-acc[j].x, -acc[j].y);
-  }
-  float2* Sp = S + size_t(p) * m;
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    if (uint32_t(j) < m && (uint32_t(j) & (G - 1u)) == gl) {
-      float2 v = acc[j];
-      if (accumulate) {
-        const float2 o = Sp[j];
-        v.x += o.x;
-        v.y += o.y;
-      }
-      Sp[j] = v;
-    }
+  float* Sp = reinterpret_cast<float*>(S + size_t(p) * m);
+  switch (G) {
+    case 4: store_sums<M, 2>(acc, gl, gmask, m, accumulate, Sp); break;
+    case 8: store_sums<M, 3>(acc, gl, gmask, m, accumulate, Sp); break;
+    case 16: store_sums<M, 4>(acc, gl, gmask, m, accumulate, Sp); break;
+    default: store_sums<M, 5>(acc, gl, gmask, m, accumulate, Sp); break;
   }
   if (gl == 0) n[p] = (accumulate ? n[p] : 0u) + (e - s);
 }
