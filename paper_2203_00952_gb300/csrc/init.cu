@@ -399,8 +399,8 @@ srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uin
   const uint32_t G = (T + D - 1u) / D;
   const size_t smem = size_t(tab.entries) * sizeof(float2) + size_t(G) * sizeof(float2) +
                       size_t(kBlock / 32) * G * sizeof(float);
-  if (smem > 48 * 1024)
-    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  // static + dynamic shared memory may exceed the 48 KB default
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int bps = 0;
   SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
   if (bps < 1) bps = 1;
@@ -422,8 +422,8 @@ srt3d_status launch_init_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const
   if (!fn) return set_error(ctx, SRT3D_EINVAL, "unsupported m");
   const size_t smem = size_t(max_entries) * sizeof(float2) + size_t(max_G) * sizeof(float2) +
                       size_t(kBlock / 32) * max_G * sizeof(float);
-  if (smem > 48 * 1024)
-    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  // static + dynamic shared memory may exceed the 48 KB default
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int bps = 0;
   SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
   if (bps < 1) bps = 1;

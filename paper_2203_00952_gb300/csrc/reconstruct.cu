@@ -1030,8 +1030,8 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   const uint32_t P = rows * cols;
   const size_t tab_smem = size_t(tab.entries) * sizeof(float2);
   const int tl = tab.two_level ? 1 : 0;
-  if (tab_smem > 48 * 1024)
-    SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+  // the static h chunk plus the table may exceed the 48 KB default
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
     k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
@@ -1122,9 +1122,8 @@ srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nfra
                        uint32_t num_groups, uint32_t total_tiles, uint32_t max_entries, uint32_t max_G,
                        const srt3d_params& prm, cudaStream_t stream) {
   const size_t tab_smem = size_t(max_entries) * sizeof(float2);
-  if (tab_smem > 48 * 1024)
-    SRT3D_CUDA_TRY(ctx,
-                   cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+  SRT3D_CUDA_TRY(ctx,
+                 cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
     k_prep_batch<<<nframes, 1024, tab_smem, stream>>>(d_frames, K);

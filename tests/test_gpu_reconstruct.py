@@ -286,7 +286,8 @@ def test_invalid_params_rejected(ctx):
         B.srt3d_reconstruct(ctx, z, n, 2, 2, T, 64, h, B.make_params(), d, a, act, a0)
 
 
-@pytest.mark.parametrize("T,m,sigma", [(8193, 12, 6.0), (65536, 32, 20.0), (64, 3, 1.5)])
+@pytest.mark.parametrize("T,m,sigma", [(8193, 12, 6.0), (65536, 32, 20.0), (64, 3, 1.5), (4613, 10, 6.0),
+                                       (8192, 16, 6.0)])
 def test_init_large_and_small_T(ctx, T, m, sigma):
     spec = synth.FrameSpec(rows=6, cols=5, T=T, sigma=sigma, mean_photons=400.0, sbr=1.0, two_surface_frac=0.5,
                            sep_lo=min(50.0, T / 8), sep_hi=min(300.0, T / 4))
