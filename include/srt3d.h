@@ -246,9 +246,15 @@ srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z, const uin
  *   h          host float [T] (read on the first chunk)
  *   chunk_stamps   host uint16 [chunk_offsets[rows*cols]], pixel-sorted
  *   chunk_offsets  host uint32 [rows*cols + 1]
- *   last_chunk 1 on the frame's final chunk
+ *   last_chunk flags: SRT3D_LAST_CHUNK on the frame's final chunk;
+ *              SRT3D_CHUNK_KEEP: the caller keeps this chunk's arrays
+ *              unchanged until the frame's srt3d_poll returns, so pinned
+ *              (page-locked) chunk arrays are uploaded asynchronously and
+ *              submit returns without waiting for the copy
  * Returns SRT3D_EBUSY (nothing consumed; retry later) when the frame cannot
- * be admitted yet. The host arrays are copied before return. */
+ * be admitted yet. Without SRT3D_CHUNK_KEEP, and for pageable arrays always,
+ * the host arrays are copied (or staged) before return. */
+enum { SRT3D_LAST_CHUNK = 1, SRT3D_CHUNK_KEEP = 2 };
 srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t rows, uint32_t cols, uint32_t T,
                           uint32_t m, const float* h, const srt3d_params* params,
                           const uint16_t* chunk_stamps, const uint32_t* chunk_offsets, int last_chunk);

@@ -223,6 +223,9 @@ def srt3d_reconstruct(ctx, z, n, rows, cols, T, m, h, params, depth, alpha, acti
     return _check(ctx, st, "srt3d_reconstruct")
 
 
+SRT3D_LAST_CHUNK, SRT3D_CHUNK_KEEP = 1, 2  # srt3d_submit flags
+
+
 def srt3d_submit(ctx, frame_id, rows, cols, T, m, h, params, chunk_stamps, chunk_offsets, last_chunk, check=True):
     st = lib().srt3d_submit(ctx, int(frame_id), int(rows), int(cols), int(T), int(m),
                             _host(h, np.float32, "h"), ctypes.byref(params),

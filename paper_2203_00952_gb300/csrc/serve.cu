@@ -297,9 +297,10 @@ extern "C" srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t
   st = launch_sketch_stream(ctx, d_st, d_off, N, P, T, m, 1, f->S, f->n, s.stream, f->flags);
   if (st != SRT3D_OK) return st;
   SRT3D_CUDA_TRY(ctx, cudaEventRecord(s.consumed[b], s.stream));
-  // the caller's arrays must be free to reuse when submit returns
-  if (direct) SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.copied[b]));
-  if (last_chunk) {
+  // the caller's arrays must be free to reuse when submit returns, unless the
+  // caller promised to keep them until the poll
+  if (direct && !(last_chunk & SRT3D_CHUNK_KEEP)) SRT3D_CUDA_TRY(ctx, cudaEventSynchronize(s.copied[b]));
+  if (last_chunk & SRT3D_LAST_CHUNK) {
     f->closed = true;
     st = launch_finalize(ctx, f->S, f->n, P, m, f->S, s.stream);
     if (st != SRT3D_OK) return st;

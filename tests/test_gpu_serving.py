@@ -98,6 +98,29 @@ def test_alone_equals_mix(sctx):
             assert np.array_equal(x, y)
 
 
+def test_kept_pinned_chunks_upload_asynchronously_with_identical_results(sctx):
+    fs = frames(3)
+    rng = np.random.default_rng(4)
+    ref, kept, pinned = [], [], []
+    for i, (fr, m, prm) in enumerate(fs):
+        ch = chunks_of(fr, 3, rng)
+        submit_all(sctx, 300 + i, fr, m, prm, ch)
+        ref.append(poll(sctx, 300 + i, fr, prm))
+        pinned.append([(torch.from_numpy(st.view(np.int16)).pin_memory().numpy().view(np.uint16),
+                        torch.from_numpy(off.view(np.int32)).pin_memory().numpy().view(np.uint32)) for st, off in ch])
+    # all frames in flight, submit returning before the uploads finish
+    for i, (fr, m, prm) in enumerate(fs):
+        h = synth.impulse_response(fr.spec.T, fr.spec.sigma).astype(np.float32)
+        for k, (st, off) in enumerate(pinned[i]):
+            flags = B.SRT3D_CHUNK_KEEP | (B.SRT3D_LAST_CHUNK if k == 2 else 0)
+            B.srt3d_submit(sctx, 400 + i, fr.spec.rows, fr.spec.cols, fr.spec.T, m, h, prm, st, off, flags)
+    for i, (fr, m, prm) in enumerate(fs):
+        kept.append(poll(sctx, 400 + i, fr, prm))
+    for a, b in zip(ref, kept):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
 def test_chunked_matches_one_shot_and_oracle_counts(sctx):
     fr, m, prm = frames(2)[1]
     rng = np.random.default_rng(2)
