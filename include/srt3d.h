@@ -81,7 +81,7 @@ typedef struct srt3d_ctx srt3d_ctx;
  * Field order and types are part of the ABI. */
 typedef struct srt3d_params {
   uint32_t iters;      /* SRT3D iterations after initialisation              */
-  uint32_t k_max;      /* surfaces per pixel, 1 or 2                         */
+  uint32_t k_max;      /* surfaces per pixel, 1..4                           */
   uint32_t radius;     /* APSS pixel window half-width, 1..3                 */
   int32_t init_mode;   /* SRT3D_INIT_MATCHED or SRT3D_INIT_GIVEN             */
   int32_t regularize;  /* 1: SRT3D (APSS + intensity smoothing);

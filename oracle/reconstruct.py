@@ -10,9 +10,11 @@ Each step is a plain array computation over all pixels, in float64:
 
   init   per pixel, matched filter s(t) = Re sum_l conj(hhat_l e^{i w_l t}) z_l
          over integer t in [0, T); t_1 = argmax (smallest t on ties),
-         alpha_1 = max(0, s(t_1) / sum_l |hhat_l|^2); with k_max = 2 the same
-         on the residual z - alpha_1 hhat e^{i w t_1}, restricted to circular
-         distance >= min_sep from t_1. A point is active iff alpha >= prune_alpha.
+         alpha_1 = max(0, s(t_1) / sum_l |hhat_l|^2); point k = 2..k_max the
+         same on the residual z - sum_{i<k} f_i hhat e^{i w t_i} (f_i = alpha_i
+         if alpha_i >= prune_alpha, else 0), restricted to circular distance
+         >= min_sep from every earlier t_i (greedy; for k_max = 2 the residual
+         of the first point). A point is active iff alpha >= prune_alpha.
   grad   Jacobi gradient step on n ||z - Psi||^2 for every active point with
          global step sizes eta_t, eta_alpha (``step_sizes``); t wraps to [0,T),
          alpha >= 0, and alpha is rescaled when sum_k alpha_k > 1.
@@ -118,15 +120,19 @@ def init_matched_filter(z, n, hh, T: int, params: Params):
         a1 = np.maximum(0.0, s[np.arange(p1 - p0), t1] / E2)
         t[p0:p1, 0] = t1
         alpha[p0:p1, 0] = a1
-        if K == 2:
-            act1 = a1 >= params.prune_alpha
-            fit = (act1 * a1)[:, None] * hh[None, :] * np.exp(1j * w[None, :] * t1[:, None])
-            s2 = matched_filter_scores(z[p0:p1] - fit, hh, T)
-            grid = np.arange(T)[None, :]
-            s2 = np.where(_circ_dist(grid, t1[:, None], T) >= params.min_sep, s2, -np.inf)
-            t2 = np.argmax(s2, axis=1)
-            t[p0:p1, 1] = t2
-            alpha[p0:p1, 1] = np.maximum(0.0, s2[np.arange(p1 - p0), t2] / E2)
+        rows = np.arange(p1 - p0)
+        grid = np.arange(T)[None, :]
+        resid = z[p0:p1].copy()
+        allowed = np.ones((p1 - p0, T), bool)
+        for k in range(1, K):
+            tk_prev, ak_prev = t[p0:p1, k - 1].astype(np.int64), alpha[p0:p1, k - 1]
+            f = np.where(ak_prev >= params.prune_alpha, ak_prev, 0.0)
+            resid = resid - f[:, None] * hh[None, :] * np.exp(1j * w[None, :] * tk_prev[:, None])
+            allowed &= _circ_dist(grid, tk_prev[:, None], T) >= params.min_sep
+            sk = np.where(allowed, matched_filter_scores(resid, hh, T), -np.inf)
+            tk = np.argmax(sk, axis=1)
+            t[p0:p1, k] = tk
+            alpha[p0:p1, k] = np.maximum(0.0, sk[rows, tk] / E2)
     active = (alpha >= params.prune_alpha) & (n > 0)[:, None]
     alpha = _project_simplex_cap(alpha, active)
     alpha0 = 1.0 - alpha.sum(axis=1)

@@ -78,7 +78,7 @@ srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint3
   if (uint64_t(rows) * cols >= (1ull << 31)) return set_error(ctx, SRT3D_EINVAL, "too many pixels");
   if (T < 2 || T > 65536) return set_error(ctx, SRT3D_EINVAL, "T must be in [2, 65536]");
   if (m < 1 || m > 32 || m >= T) return set_error(ctx, SRT3D_EINVAL, "m must be in [1, min(32, T-1)]");
-  if (prm->k_max < 1 || prm->k_max > 2) return set_error(ctx, SRT3D_EINVAL, "k_max must be 1 or 2");
+  if (prm->k_max < 1 || prm->k_max > 4) return set_error(ctx, SRT3D_EINVAL, "k_max must be 1..4");
   if (prm->radius < 1 || prm->radius > 3) return set_error(ctx, SRT3D_EINVAL, "radius must be 1..3");
   if (prm->init_mode != SRT3D_INIT_MATCHED && prm->init_mode != SRT3D_INIT_GIVEN)
     return set_error(ctx, SRT3D_EINVAL, "unknown init_mode");

@@ -1,9 +1,10 @@
 // Sketched matched-filter initialisation (Sec. 3): for each pixel, the first
 // point is the integer t maximising
 //   s(t) = Re sum_{l=1}^{m} c_l e^{-i w_l t},   c_l = conj(hhat_l) z_l,
-// with alpha = s / sum_l |hhat_l|^2; with K = 2 the second point maximises the
-// same score of the residual z - alpha_1 hhat e^{i w t_1} at least min_sep bins
-// away from t_1 (circularly).
+// with alpha = s / sum_l |hhat_l|^2; point k = 2..K maximises the same score of
+// the residual z - sum_{i<k} f_i hhat e^{i w t_i} (f_i = alpha_i if it reaches
+// prune_alpha, else 0) at least min_sep bins (circularly) from every earlier
+// t_i (greedy passes; K <= 4).
 //
 // One warp per pixel. The coefficients c_l live in registers, zero-padded to
 // the kernel's harmonic count M (Horner with leading zero coefficients gives
@@ -63,10 +64,23 @@ __device__ __forceinline__ float2 mf_score2(const float2 (&cx)[M], const float2 
   return ffma2(ax, wx, fmul2(ay, nwy));
 }
 
-__device__ __forceinline__ bool mf_allowed(uint32_t t, int excl_t, float min_sep, uint32_t T) {
-  if (excl_t < 0) return true;
-  const uint32_t d0 = t > uint32_t(excl_t) ? t - uint32_t(excl_t) : uint32_t(excl_t) - t;
-  return float(min(d0, T - d0)) >= min_sep;
+// Exclusion zones of a later pass: the NX earlier depths, and the least
+// circular distance min_sep a candidate keeps from each.
+template <int NX>
+struct Excl {
+  uint32_t t[NX > 0 ? NX : 1];
+  float min_sep;
+};
+
+template <int NX>
+__device__ __forceinline__ bool mf_allowed(uint32_t t, const Excl<NX>& ex, uint32_t T) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < NX; ++i) {
+    const uint32_t d0 = t > ex.t[i] ? t - ex.t[i] : ex.t[i] - t;
+    ok = ok && float(min(d0, T - d0)) >= ex.min_sep;
+  }
+  return ok;
 }
 
 __device__ __forceinline__ void mf_take(float s, uint32_t t, float& bs, uint32_t& bt) {
@@ -101,10 +115,10 @@ uint32_t mf_grid_spacing_impl(uint32_t T, uint32_t m) {
 // across the warp's lanes. Every t whose FP32 score can be the maximum is
 // evaluated with the same arithmetic as an exhaustive scan, so the result
 // equals the exhaustive FP32 argmax.
-template <int M>
+template <int M, int NX>
 __device__ __forceinline__ void warp_argmax_scores(float2 mine, const float2 (&cx)[M], const float2 (&cy)[M],
                                                    uint32_t T, const float2* s_tab, bool tl, const float2* s_wg,
-                                                   float* s_grid, uint32_t D, uint32_t G, int excl_t, float min_sep,
+                                                   float* s_grid, uint32_t D, uint32_t G, const Excl<NX>& ex,
                                                    float* best_s, uint32_t* best_t) {
   const uint32_t lane = threadIdx.x & 31u;
   // M0 = sum |c_l|, M2 = sum |c_l| w_l^2 (lane l holds c_{l+1}, zero beyond m)
@@ -118,7 +132,7 @@ __device__ __forceinline__ void warp_argmax_scores(float2 mine, const float2 (&c
   if (m0 == 0.f) {  // all scores are exactly 0: the smallest allowed t wins
     for (uint32_t t0 = 0; t0 < T; t0 += 32u) {
       const uint32_t t = t0 + lane;
-      const unsigned ok = __ballot_sync(0xffffffffu, t < T && mf_allowed(t, excl_t, min_sep, T));
+      const unsigned ok = __ballot_sync(0xffffffffu, t < T && mf_allowed<NX>(t, ex, T));
       if (ok) {
         *best_s = 0.f;
         *best_t = t0 + uint32_t(__ffs(ok)) - 1u;
@@ -139,10 +153,10 @@ __device__ __forceinline__ void warp_argmax_scores(float2 mine, const float2 (&c
     const bool two = g2 < G;
     const float2 sg = mf_score2<M>(cx, cy, s_wg[g], s_wg[two ? g2 : g]);
     s_grid[g] = sg.x;
-    if (mf_allowed(g * D, excl_t, min_sep, T)) mf_take(sg.x, g * D, bs, bt);
+    if (mf_allowed<NX>(g * D, ex, T)) mf_take(sg.x, g * D, bs, bt);
     if (two) {
       s_grid[g2] = sg.y;
-      if (mf_allowed(g2 * D, excl_t, min_sep, T)) mf_take(sg.y, g2 * D, bs, bt);
+      if (mf_allowed<NX>(g2 * D, ex, T)) mf_take(sg.y, g2 * D, bs, bt);
     }
   }
   __syncwarp();
@@ -172,7 +186,7 @@ __device__ __forceinline__ void warp_argmax_scores(float2 mine, const float2 (&c
         const uint32_t len = min(D, T - a);
         if (off == 0u || off >= len) continue;
         const uint32_t t = a + off;
-        if (!mf_allowed(t, excl_t, min_sep, T)) continue;
+        if (!mf_allowed<NX>(t, ex, T)) continue;
         mf_take(mf_score<M>(cx, cy, phase(s_tab, t, tl)), t, bs, bt);
       }
     }
@@ -199,6 +213,47 @@ __device__ __forceinline__ void broadcast_c(float2 mine, float2 (&cx)[M], float2
   }
 }
 
+// Passes k .. K-1 of a pixel (lane l < m holds the residual r_l of the
+// earlier passes, starting from z_l): subtract point k-1's fit, score
+// conj(hhat) r, take the argmax outside the earlier points' exclusion zones.
+template <int K, int M, int k>
+__device__ __forceinline__ void later_passes(uint32_t lane, uint32_t m, uint32_t cnt, uint32_t T, float invT,
+                                             const float2* s_tab, bool tl, const float2* s_wg, float* s_grid,
+                                             uint32_t D, uint32_t G, const float2* s_hh, float E2, float prune_alpha,
+                                             float min_sep, float2 r, float2 (&cx)[M], float2 (&cy)[M],
+                                             float (&a)[K], float (&t)[K], uint32_t (&ti)[K], bool (&act)[K]) {
+  if constexpr (k < K) {
+    float2 mine = make_float2(0.f, 0.f);
+    if (lane < m) {
+      const float2 hv = s_hh[lane];
+      const float2 e = phase(s_tab, mulmod(lane + 1u, ti[k - 1], T, invT), tl);
+      const float f = (a[k - 1] >= prune_alpha) ? a[k - 1] : 0.f;
+      const float2 fit = cmul(hv, e);
+      r = make_float2(r.x - f * fit.x, r.y - f * fit.y);
+      mine = cmul(make_float2(hv.x, -hv.y), r);
+    }
+    broadcast_c<M>(mine, cx, cy);
+    __syncwarp();
+    Excl<k> ex;
+#pragma unroll
+    for (int i = 0; i < k; ++i) ex.t[i] = ti[i];
+    ex.min_sep = min_sep;
+    float sk;
+    uint32_t tk;
+    warp_argmax_scores<M, k>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, ex, &sk, &tk);
+    if (tk >= T) {
+      tk = 0u;
+      sk = 0.f;
+    }
+    a[k] = fmaxf(0.f, sk / E2);
+    t[k] = float(tk);
+    ti[k] = tk;
+    act[k] = (a[k] >= prune_alpha) && cnt > 0;
+    later_passes<K, M, k + 1>(lane, m, cnt, T, invT, s_tab, tl, s_wg, s_grid, D, G, s_hh, E2, prune_alpha, min_sep,
+                              r, cx, cy, a, t, ti, act);
+  }
+}
+
 // Matched-filter initialisation of pixel p by one warp.
 template <int K, int M>
 __device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict__ z, const uint32_t* __restrict__ n,
@@ -219,39 +274,20 @@ __device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict_
   broadcast_c<M>(mine, cx, cy);
   float s1;
   uint32_t t1;
-  warp_argmax_scores<M>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, -1, 0.f, &s1, &t1);
+  warp_argmax_scores<M, 0>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, Excl<0>{{0u}, 0.f}, &s1, &t1);
   if (t1 >= T) {  // no finite score (cannot happen for finite z)
     t1 = 0u;
     s1 = 0.f;
   }
   float a[K], t[K];
   bool act[K];
+  uint32_t ti[K];
   a[0] = fmaxf(0.f, s1 / E2);
   t[0] = float(t1);
+  ti[0] = t1;
   act[0] = (a[0] >= prune_alpha) && cnt > 0;
-  if (K == 2) {
-    mine = make_float2(0.f, 0.f);
-    if (lane < m) {
-      const float2 hv = s_hh[lane];
-      const float2 e = phase(s_tab, mulmod(lane + 1u, t1, T, invT), tl);
-      const float f = (a[0] >= prune_alpha) ? a[0] : 0.f;
-      const float2 fit = cmul(hv, e);
-      const float2 r = make_float2(zl.x - f * fit.x, zl.y - f * fit.y);
-      mine = cmul(make_float2(hv.x, -hv.y), r);
-    }
-    broadcast_c<M>(mine, cx, cy);
-    __syncwarp();
-    float s2;
-    uint32_t t2;
-    warp_argmax_scores<M>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, int(t1), min_sep, &s2, &t2);
-    if (t2 >= T) {
-      t2 = 0u;
-      s2 = 0.f;
-    }
-    a[K - 1] = fmaxf(0.f, s2 / E2);
-    t[K - 1] = float(t2);
-    act[K - 1] = (a[K - 1] >= prune_alpha) && cnt > 0;
-  }
+  later_passes<K, M, 1>(lane, m, cnt, T, invT, s_tab, tl, s_wg, s_grid, D, G, s_hh, E2, prune_alpha, min_sep, zl,
+                        cx, cy, a, t, ti, act);
   float sum = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -393,7 +429,7 @@ srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uin
                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
                          cudaStream_t stream) {
   const int M = init_round_m(m);
-  InitFn fn = K == 1 ? init_fn<1>(M) : init_fn<2>(M);
+  InitFn fn = K == 1 ? init_fn<1>(M) : K == 2 ? init_fn<2>(M) : K == 3 ? init_fn<3>(M) : init_fn<4>(M);
   if (!fn) return set_error(ctx, SRT3D_EINVAL, "unsupported m");
   const uint32_t D = mf_grid_spacing_impl(T, m);
   const uint32_t G = (T + D - 1u) / D;
@@ -418,7 +454,10 @@ srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uin
 srt3d_status launch_init_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const uint3* d_items,
                                uint32_t num_items, uint32_t K, int M, uint32_t max_entries, uint32_t max_G,
                                const srt3d_params& prm, cudaStream_t stream) {
-  InitBatchFn fn = K == 1 ? init_batch_fn<1>(M) : init_batch_fn<2>(M);
+  InitBatchFn fn = K == 1   ? init_batch_fn<1>(M)
+                   : K == 2 ? init_batch_fn<2>(M)
+                   : K == 3 ? init_batch_fn<3>(M)
+                            : init_batch_fn<4>(M);
   if (!fn) return set_error(ctx, SRT3D_EINVAL, "unsupported m");
   const size_t smem = size_t(max_entries) * sizeof(float2) + size_t(max_G) * sizeof(float2) +
                       size_t(kBlock / 32) * max_G * sizeof(float);

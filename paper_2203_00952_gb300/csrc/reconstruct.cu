@@ -614,7 +614,7 @@ __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, in
           int cnt = 0;
           // branch-free: every slot is loaded and weighted (0 for non-neighbours),
           // which leaves the sums exactly as if the slot were skipped
-#pragma unroll
+#pragma unroll(K <= 2 ? 2 * R + 1 : 1)
           for (int dr = -R; dr <= R; ++dr)
 #pragma unroll
             for (int dc = -R; dc <= R; ++dc) {
@@ -684,7 +684,7 @@ __device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, in
       if (!sm.act[q0][k]) continue;
       float Sw = 0, Spx = 0, Spy = 0, Spz = 0, Snx = 0, Sny = 0, Snz = 0, Spn = 0, Spp = 0, Swa = 0;
       int cnt = 0;
-#pragma unroll
+#pragma unroll(K <= 2 ? 2 * R + 1 : 1)
       for (int dr = -R; dr <= R; ++dr)
 #pragma unroll
         for (int dc = -R; dc <= R; ++dc) {
@@ -991,6 +991,11 @@ template <int K, int R>
 srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const float2* z, const uint32_t* n,
                                     uint32_t T, uint32_t m, const Scratch& sc, float* depth, float* alpha,
                                     uint8_t* active, float* alpha0, uint32_t iters, cudaStream_t stream) {
+  if constexpr (K > 2 && R > 1) {
+    // three or four points per pixel at radius > 1 do not fit two CTAs per SM:
+    // the caller launches per iteration
+    return SRT3D_EAGAIN;
+  } else {
   constexpr int H = 2 * R;
   constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
   const size_t zsmem = size_t(RH) * RW * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
@@ -1021,6 +1026,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
                                                   args, zsmem, stream));
   prof_end(ctx, KID_ITER_ALL, mk, stream);
   return SRT3D_OK;
+  }
 }
 
 template <int K>
@@ -1172,11 +1178,20 @@ srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames
                                       const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
                                       uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
                                       cudaStream_t stream) {
-  if (prm.k_max == 1)
-    return run_batch<1>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                        stream);
-  return run_batch<2>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                      stream);
+  switch (prm.k_max) {
+    case 1:
+      return run_batch<1>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                          stream);
+    case 2:
+      return run_batch<2>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                          stream);
+    case 3:
+      return run_batch<3>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                          stream);
+    default:
+      return run_batch<4>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
+                          stream);
+  }
 }
 
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
@@ -1197,8 +1212,12 @@ srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n
   srt3d_status st = get_phase_table(ctx, T, &tab);
   if (st != SRT3D_OK) return st;
   const Scratch sc = carve(scratch, P, prm.k_max);
-  if (prm.k_max == 1) return run<1>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
-  return run<2>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+  switch (prm.k_max) {
+    case 1: return run<1>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+    case 2: return run<2>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+    case 3: return run<3>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+    default: return run<4>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+  }
 }
 
 }  // namespace srt3d
@@ -1312,7 +1331,10 @@ extern "C" srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   const Scratch sc = carve(base, P, params->k_max);
   const float2* zz = reinterpret_cast<const float2*>(z);
-  if (params->k_max == 1)
-    return run<1>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
-  return run<2>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+  switch (params->k_max) {
+    case 1: return run<1>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+    case 2: return run<2>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+    case 3: return run<3>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+    default: return run<4>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+  }
 }

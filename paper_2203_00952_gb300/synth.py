@@ -159,6 +159,41 @@ def make_stream_frame(spec: FrameSpec, seed: int, frame: int = 0) -> StreamFrame
     return StreamFrame(spec=spec, stamps=stamps, offsets=offsets.astype(np.uint32), truth=truth)
 
 
+def make_multi_surface_frame(spec: FrameSpec, n_surf: int, seed: int, frame: int = 0) -> StreamFrame:
+    """Stream frame with n_surf surfaces in every pixel (the multi-surface
+    scenes of Sec. 4, beyond two): the first at the depth map of make_truth,
+    each next one U(sep_lo, sep_hi) bins further (mod T), reflectivities
+    U(0.2, 1); Poisson counts with the same signal/background rates as
+    make_stream_frame (mean over pixels of sum r = 0.6 n_surf), photons thinned
+    into surfaces and background, signal stamps round(t + sigma N(0,1)) mod T.
+    truth.depth / refl / alpha are [P, n_surf]."""
+    rng = np.random.default_rng(frame_seed(seed, frame))
+    P, T = spec.num_pixels, spec.T
+    depth = np.empty((P, n_surf))
+    depth[:, 0] = _depth_map(spec)
+    for k in range(1, n_surf):
+        depth[:, k] = np.mod(depth[:, k - 1] + rng.uniform(spec.sep_lo, spec.sep_hi, size=P), T)
+    refl = rng.uniform(0.2, 1.0, size=(P, n_surf))
+    B = spec.mean_photons / (1.0 + spec.sbr)
+    S = spec.mean_photons * spec.sbr / ((1.0 + spec.sbr) * 0.6 * n_surf)
+    lam = S * refl.sum(axis=1) + B
+    alpha = S * refl / lam[:, None]
+    truth = Truth(depth=depth, refl=refl, nsurf=np.full(P, n_surf, np.int8), alpha=alpha, alpha0=B / lam)
+    counts = rng.poisson(lam).astype(np.int64)
+    offsets = np.zeros(P + 1, dtype=np.int64)
+    np.cumsum(counts, out=offsets[1:])
+    stamps = np.empty(int(offsets[-1]), dtype=np.uint16)
+    cum = np.cumsum(alpha, axis=1)
+    pix = np.repeat(np.arange(P), counts)
+    u = rng.uniform(size=pix.size)
+    g = rng.standard_normal(size=pix.size)
+    bg = rng.integers(0, T, size=pix.size)
+    k = (u[:, None] >= cum[pix]).sum(axis=1)  # surface index, n_surf = background
+    sig = np.mod(np.rint(depth[pix, np.minimum(k, n_surf - 1)] + spec.sigma * g).astype(np.int64), T)
+    stamps[:] = np.where(k < n_surf, sig, bg).astype(np.uint16)
+    return StreamFrame(spec=spec, stamps=stamps, offsets=offsets.astype(np.uint32), truth=truth)
+
+
 def make_hist_frame(spec: FrameSpec, seed: int, frame: int = 0):
     """uint16 histograms [P, T] (one bin per integer stamp) and the truth."""
     rng = np.random.default_rng(frame_seed(seed, frame))

@@ -124,19 +124,70 @@ def check_init_validity(t_g, a_g, act_g, z, n_np, hh, T, p: Params):
     ok = act_g[:, 0] & (a1_sum < 1 - 1e-6)
     if p.k_max == 1:
         assert np.allclose(a_g[ok, 0], a1_ref[ok], atol=1e-6, rtol=1e-5)
-    if p.k_max == 2:
-        w = 2 * np.pi * np.arange(1, hh.size + 1) / T
-        # residual with the GPU's first surface at its pre-rescale intensity
-        f = np.where(a1_ref >= p.prune_alpha, a1_ref, 0.0)
-        r = z - f[:, None] * hh[None, :] * np.exp(1j * w[None, :] * t1[:, None])
-        s2 = oracle.matched_filter_scores(r, hh, T)
-        d = np.abs(np.arange(T)[None, :] - t1[:, None]) % T
-        d = np.minimum(d, T - d)
-        s2 = np.where(d >= p.min_sep, s2, -np.inf)
-        t2 = t_g[:, 1].astype(np.int64)
-        scale2 = np.sum(np.abs(r * np.conj(hh)[None, :]), axis=1)
-        valid2 = s2[idx, t2] >= s2.max(axis=1) - (1e-5 * scale2 + 1e-7 + 1e-5 * scale)
-        assert valid2.all(), f"{np.count_nonzero(~valid2)} invalid second argmaxes"
+    # later points: greedy passes on the residual of the earlier points (at
+    # their pre-rescale intensities), outside every earlier exclusion zone
+    w = 2 * np.pi * np.arange(1, hh.size + 1) / T
+    r = z.copy()
+    allowed = np.ones((P, T), bool)
+    tol_acc = 1e-5 * scale
+    a_prev, t_prev = a1_ref, t1
+    for k in range(1, p.k_max):
+        f = np.where(a_prev >= p.prune_alpha, a_prev, 0.0)
+        r = r - f[:, None] * hh[None, :] * np.exp(1j * w[None, :] * t_prev[:, None])
+        d = np.abs(np.arange(T)[None, :] - t_prev[:, None]) % T
+        allowed &= np.minimum(d, T - d) >= p.min_sep
+        sk = np.where(allowed, oracle.matched_filter_scores(r, hh, T), -np.inf)
+        tk = t_g[:, k].astype(np.int64)
+        scale_k = np.sum(np.abs(r * np.conj(hh)[None, :]), axis=1)
+        tol_acc = tol_acc + 1e-5 * scale_k
+        validk = sk[idx, tk] >= sk.max(axis=1) - (tol_acc + 1e-7)
+        assert validk.all(), f"{np.count_nonzero(~validk)} invalid argmaxes of pass {k + 1}"
+        a_prev, t_prev = np.maximum(0.0, sk[idx, tk] / E2), tk
+
+
+def multi_surface_inputs(ctx, K, seed, m=20, rows=24, cols=28):
+    # surfaces 300-700 bins apart: resolvable with m = 20 harmonics (lobe
+    # width ~ T/m = 205 bins)
+    spec = synth.FrameSpec(rows=rows, cols=cols, T=4096, sigma=6.0, mean_photons=1500.0, sbr=1.0, sep_lo=300.0,
+                           sep_hi=700.0)
+    fr = synth.make_multi_surface_frame(spec, K, seed)
+    z, n = sketch_frame(ctx, fr, m)
+    h32 = synth.impulse_response(spec.T, spec.sigma).astype(np.float32)
+    hh = oracle.h_hat(h32.astype(np.float64), m)
+    return fr, spec, z, n, to_complex(z), counts(n), h32, hh
+
+
+@pytest.mark.parametrize("K", [3, 4])
+def test_init_matched_filter_more_surfaces(ctx, K):
+    fr, spec, z, n, z_np, n_np, h32, hh = multi_surface_inputs(ctx, K, 70 + K)
+    p = oracle_params(iters=0, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, 20, h32, p)
+    check_init_validity(g[0], g[1], g[2], z_np, n_np, hh, spec.T, p)
+    np.testing.assert_allclose(g[3], 1 - g[1].sum(axis=1), atol=1e-6)
+    # the K true surfaces are found: each within 3 sigma of some active point
+    d = np.abs(g[0][:, :, None] - fr.truth.depth[:, None, :])
+    d = np.minimum(d, spec.T - d)
+    found = (np.where(g[2][:, :, None], d, np.inf).min(axis=1) <= 3 * spec.sigma)
+    assert found.mean() > 0.8
+
+
+@pytest.mark.parametrize("K", [3, 4])
+def test_iterations_more_surfaces(ctx, K):
+    # one iteration from a shared state, then 10 from the oracle's init
+    fr, spec, z, n, z_np, n_np, h32, hh = multi_surface_inputs(ctx, K, 80 + K)
+    m = 20
+    p = oracle_params(iters=1, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+    s0 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, iters=3)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=s0[:3], iters=1)
+    eta = oracle.step_sizes(hh, n_np.max(), K, spec.T)
+    r = oracle.iterate(z_np, n_np, s0[0], s0[1], s0[2], hh, spec.T, spec.rows, spec.cols, p, *eta)
+    compare_state(g, r, n_np, 1e-3, 1e-4, FLIP_FRAC, f"one iteration, K = {K}", spec.T)
+    p10 = oracle_params(iters=10, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+    init = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p10)[:3]
+    g10 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p10, init=init)
+    r10 = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p10, init=init)
+    compare_state(g10, r10, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, f"10 iterations, K = {K}", spec.T,
+                  outlier_frac=2e-3)
 
 
 @pytest.mark.parametrize("K", [1, 2])
@@ -276,7 +327,7 @@ def test_invalid_params_rejected(ctx):
     a = torch.zeros(4, 2, device="cuda")
     act = torch.zeros(4, 2, dtype=torch.uint8, device="cuda")
     a0 = torch.zeros(4, device="cuda")
-    for kw in (dict(k_max=3), dict(radius=0), dict(radius=4), dict(apss_h=0.0), dict(smooth_lambda=1.5),
+    for kw in (dict(k_max=5), dict(k_max=0), dict(radius=0), dict(radius=4), dict(apss_h=0.0), dict(smooth_lambda=1.5),
                dict(d_max=2e6), dict(depth_scale=2e3)):
         prm = B.make_params(**kw)
         with pytest.raises(B.SRT3DError) as ei:

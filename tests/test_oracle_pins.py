@@ -244,6 +244,42 @@ def test_init_two_surfaces_with_delta_pulse_full_band():
     assert active.all()
 
 
+@pytest.mark.parametrize("truth_t,truth_a", [([10, 30, 50], [0.4, 0.3, 0.2]),
+                                             ([5, 20, 37, 55], [0.3, 0.25, 0.2, 0.15])])
+def test_init_k_surfaces_with_delta_pulse_full_band(truth_t, truth_a):
+    # delta pulse and m = T - 1: per unit alpha the matched filter is T - 1 at
+    # a surface and -1 elsewhere, so each greedy pass finds the largest
+    # remaining surface exactly (the residual of the earlier passes is off by
+    # O(1/T) in alpha only)
+    T = 64
+    h = np.zeros(T)
+    h[0] = 1.0
+    m = T - 1
+    hh = oracle.h_hat(h, m)
+    K = len(truth_t)
+    y = _expected_hist(T, h, truth_t, truth_a, 1.0 - sum(truth_a), 1.0)
+    z = _sketch_real(y, m)
+    t, alpha, active, _ = oracle.init_matched_filter(z, np.array([1]), hh, T, Params(k_max=K, min_sep=3))
+    assert t[0].tolist() == truth_t
+    np.testing.assert_allclose(alpha[0], truth_a, atol=2.0 / T)
+    assert active.all()
+
+
+def test_init_exclusion_covers_every_earlier_point():
+    # three surfaces 2 bins apart with min_sep 3: after the first pass the
+    # other two lie inside its exclusion zone, so passes 2 and 3 must land
+    # >= 3 bins from each earlier point
+    T = 64
+    h = np.zeros(T)
+    h[0] = 1.0
+    hh = oracle.h_hat(h, T - 1)
+    y = _expected_hist(T, h, [20, 22, 24], [0.3, 0.3, 0.3], 0.1, 1.0)
+    t, _, _, _ = oracle.init_matched_filter(_sketch_real(y, T - 1), np.array([1]), hh, T, Params(k_max=3, min_sep=3))
+    d = np.abs(t[0][:, None] - t[0][None, :])
+    d = np.minimum(d, T - d)
+    assert np.all(d[~np.eye(3, dtype=bool)] >= 3)
+
+
 def test_init_empty_pixel_has_no_points():
     T, m = 64, 4
     hh = oracle.h_hat(synth.impulse_response(T, 2.0), m)
