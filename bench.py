@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
-    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch"], default="all")
+    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces"], default="all")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -246,6 +246,72 @@ def hist_section(B, ctx, dev, steps, flush):
     del hist, S, n
     torch.cuda.empty_cache()
     return out
+
+
+# ----------------------------------------------------------------- K = 3
+SURF = dict(rows=256, cols=256, T=4096, sigma=6.0, mean_photons=1500.0, sbr=1.0, sep_lo=300.0, sep_hi=700.0,
+            n_surf=3, m=20, iters=30)
+
+
+def surfaces_section(B, ctx, dev, steps, flush):
+    """Three surfaces per pixel (k_max = 3): a 256x256 frame with three
+    surfaces 300-700 bins apart in every pixel, m = 20, 30 iterations; the
+    whole step (sketch, finalize, reconstruct) timed with CUDA events, L2
+    evicted between steps, and the recovery of the true surfaces."""
+    import numpy as np
+    import torch
+
+    from paper_2203_00952_gb300 import synth
+
+    w = SURF
+    spec = synth.FrameSpec(rows=w["rows"], cols=w["cols"], T=w["T"], sigma=w["sigma"],
+                           mean_photons=w["mean_photons"], sbr=w["sbr"], sep_lo=w["sep_lo"], sep_hi=w["sep_hi"])
+    fr = synth.make_multi_surface_frame(spec, w["n_surf"], synth.SEED_256x256 + 7)
+    P, T, m, K = spec.num_pixels, spec.T, w["m"], w["n_surf"]
+    N = int(fr.offsets[-1])
+    stamps = torch.from_numpy(fr.stamps.view(np.int16)).to(dev)
+    offsets = torch.from_numpy(fr.offsets.view(np.int32)).to(dev)
+    S = torch.empty(P, m, 2, device=dev)
+    n = torch.empty(P, dtype=torch.int32, device=dev)
+    depth = torch.empty(P, K, device=dev)
+    alpha = torch.empty(P, K, device=dev)
+    active = torch.empty(P, K, dtype=torch.uint8, device=dev)
+    alpha0 = torch.empty(P, device=dev)
+    h = torch.from_numpy(synth.impulse_response(T, spec.sigma).astype(np.float32)).to(dev)
+    prm = B.make_params(iters=w["iters"], k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        B.srt3d_sketch_stream(ctx, stamps, offsets, T, m, 0, S, n, stream)
+        B.srt3d_finalize(ctx, S, n, m, S, stream)
+        B.srt3d_reconstruct(ctx, S, n, spec.rows, spec.cols, T, m, h, prm, depth, alpha, active, alpha0, stream)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(dev)
+    B.srt3d_profile_enable(ctx, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    st = B.srt3d_sync(ctx, stream, check=False)
+    prof = B.profile_totals(ctx)
+    B.srt3d_profile_enable(ctx, False)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    d = depth.cpu().numpy()
+    act = active.cpu().numpy().astype(bool)
+    err = np.abs(d[:, :, None] - fr.truth.depth[:, None, :])
+    err = np.minimum(err, T - err)
+    found = float(np.mean(np.where(act[:, :, None], err, np.inf).min(axis=1) <= 3 * spec.sigma))
+    del stamps, offsets, S, n, depth, alpha, active, alpha0
+    torch.cuda.empty_cache()
+    return {"workload": f"srt3d_256x256_T4096_m20_K3_it30_three_surfaces", "photons_per_frame": N,
+            "ms_per_step": ms, "photons_per_s": N / (ms / 1e3), "frames_per_s": 1e3 / ms,
+            "kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}, "surfaces_found_within_3sigma": found,
+            "device_status": int(st)}
 
 
 # ----------------------------------------------------------------- serving
@@ -524,6 +590,14 @@ def gpu_arm(args):
         if rank == 0:
             print(json.dumps({"batch": res}), flush=True)
         return
+    if args.only == "surfaces":
+        ctx = B.srt3d_create(local)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        res = surfaces_section(B, ctx, dev, args.batch_steps, flush)
+        B.srt3d_destroy(ctx)
+        if rank == 0:
+            print(json.dumps({"surfaces": res}), flush=True)
+        return
     if args.only == "hist":
         # histogram path alone (for profiling): no step timing, no baseline
         ctx = B.srt3d_create(local)
@@ -657,13 +731,14 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
     d2h = sum(o.nbytes for o in outs if o is not None)
 
-    hist = batch = None
+    hist = batch = surfaces = None
     if args.only in ("all", "hist") and rank == 0:
         hist = hist_section(B, ctx, dev, args.hist_steps, flush)
     if args.only == "all" and rank == 0:
         del stamps, offsets, S, z
         torch.cuda.empty_cache()
         batch = batch_section(B, ctx, dev, args.batch_steps, flush)
+        surfaces = surfaces_section(B, ctx, dev, args.batch_steps, flush)
     B.srt3d_destroy(ctx)
     serving = None
     if args.only == "all" and rank == 0 and world == 1:
@@ -738,6 +813,7 @@ def gpu_arm(args):
         "cpu_baseline": cpu,
         "hist_sketch": hist,
         "batch": batch,
+        "surfaces": surfaces,
         "serving": serving,
     }
     print(json.dumps(out), flush=True)

@@ -184,13 +184,18 @@ def make_multi_surface_frame(spec: FrameSpec, n_surf: int, seed: int, frame: int
     np.cumsum(counts, out=offsets[1:])
     stamps = np.empty(int(offsets[-1]), dtype=np.uint16)
     cum = np.cumsum(alpha, axis=1)
-    pix = np.repeat(np.arange(P), counts)
-    u = rng.uniform(size=pix.size)
-    g = rng.standard_normal(size=pix.size)
-    bg = rng.integers(0, T, size=pix.size)
-    k = (u[:, None] >= cum[pix]).sum(axis=1)  # surface index, n_surf = background
-    sig = np.mod(np.rint(depth[pix, np.minimum(k, n_surf - 1)] + spec.sigma * g).astype(np.int64), T)
-    stamps[:] = np.where(k < n_surf, sig, bg).astype(np.uint16)
+    for p0 in range(0, P, BLOCK_PIXELS):
+        p1 = min(P, p0 + BLOCK_PIXELS)
+        lo, hi = int(offsets[p0]), int(offsets[p1])
+        if hi == lo:
+            continue
+        pix = np.repeat(np.arange(p0, p1), counts[p0:p1])
+        u = rng.uniform(size=hi - lo)
+        g = rng.standard_normal(size=hi - lo)
+        bg = rng.integers(0, T, size=hi - lo)
+        k = (u[:, None] >= cum[pix]).sum(axis=1)  # surface index; n_surf = background
+        sig = np.mod(np.rint(depth[pix, np.minimum(k, n_surf - 1)] + spec.sigma * g).astype(np.int64), T)
+        stamps[lo:hi] = np.where(k < n_surf, sig, bg).astype(np.uint16)
     return StreamFrame(spec=spec, stamps=stamps, offsets=offsets.astype(np.uint32), truth=truth)
 
 
