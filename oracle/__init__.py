@@ -24,7 +24,17 @@ from .sketch import (  # noqa: F401
     finalize,
     merge_states,
 )
-from .model import h_hat, model_cf, sketched_loss, sketched_gradient  # noqa: F401
+from .model import (  # noqa: F401
+    h_hat,
+    model_cf,
+    sketched_loss,
+    sketched_gradient,
+    sigma_theta,
+    weighting_matrix,
+    weighted_loss,
+    weighted_gradient,
+    SIGMA_RIDGE,
+)
 from .reconstruct import (  # noqa: F401
     Params,
     step_sizes,

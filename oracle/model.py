@@ -1,5 +1,5 @@
 """Oracle: characteristic function of the observation model and the sketched
-loss (Sec. 2, Eqs. 1, 4, 6; Sec. 3, Eq. 8 with W = I).
+loss (Sec. 2, Eqs. 1, 4, 5, 6; Sec. 3, Eq. 8 with W = I or W = Sigma^-1).
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
@@ -72,4 +72,58 @@ def sketched_gradient(z, n, t, alpha, active, hh, T: int):
     nn = np.asarray(n, dtype=np.float64)[:, None]
     g_t = -2.0 * nn * np.sum(np.real(np.conj(r)[:, None, :] * dpsi_dt), axis=2)
     g_a = -2.0 * nn * np.sum(np.real(np.conj(r)[:, None, :] * dpsi_da), axis=2)
+    return np.where(act, g_t, 0.0), np.where(act, g_a, 0.0)
+
+
+# Ridge added to Sigma_theta before inverting it (Sigma_theta is singular for a
+# noise-free point mass, alpha_0 = 0); a reading, the paper gives none.
+SIGMA_RIDGE = 1e-3
+
+
+def sigma_theta(t, alpha, active, hh, T: int) -> np.ndarray:
+    """Sigma_theta of Eq. 5: the covariance of the vector (exp(i w_l x))_l,
+    l = 1..m, for one photon x drawn from the model (Eq. 1), read as the
+    Hermitian covariance
+        Sigma_jk = Psi(w_j - w_k) - Psi(w_j) conj(Psi(w_k)),
+    with Psi(0) = 1, Psi(w_{-d}) = conj(Psi(w_d)) and Psi(w_d) = Psi_d of
+    model_cf for d >= 1 (the background vanishes at nonzero harmonics).
+    Returns complex128 [P, m, m]."""
+    psi = model_cf(t, alpha, active, hh, T)  # [P, m]
+    P, m = psi.shape
+    d = np.arange(m)[:, None] - np.arange(m)[None, :]  # j - k
+    full = np.concatenate([np.conj(psi[:, ::-1]), np.ones((P, 1)), psi], axis=1)  # Psi_d, d = -m..m
+    toep = full[:, d + m]  # Psi(w_j - w_k); index d + m maps d = 0 to the column of ones
+    return toep - psi[:, :, None] * np.conj(psi)[:, None, :]
+
+
+def weighting_matrix(t, alpha, active, hh, T: int) -> np.ndarray:
+    """W = (Sigma_theta + SIGMA_RIDGE I)^-1 (the precision matrix of Eq. 6),
+    [P, m, m]."""
+    S = sigma_theta(t, alpha, active, hh, T)
+    m = S.shape[1]
+    return np.linalg.inv(S + SIGMA_RIDGE * np.eye(m)[None])
+
+
+def weighted_loss(z, n, t, alpha, active, hh, T: int, W) -> np.ndarray:
+    """Per-pixel n (z - Psi)^H W (z - Psi) (Eq. 6 with a given W [P, m, m])."""
+    r = np.asarray(z) - model_cf(t, alpha, active, hh, T)
+    return np.asarray(n, dtype=np.float64) * np.real(np.einsum("pj,pjk,pk->p", np.conj(r), W, r))
+
+
+def weighted_gradient(z, n, t, alpha, active, hh, T: int, W):
+    """Gradient of weighted_loss with W held fixed: with r = z - Psi and
+    v = W r,  dL/dtheta = -2 n Re( sum_l conj(dPsi_l/dtheta) v_l ), i.e. the
+    W = I gradient of sketched_gradient with r replaced by v."""
+    t = np.asarray(t, dtype=np.float64)
+    act = np.asarray(active, dtype=bool)
+    a = np.where(act, np.asarray(alpha, dtype=np.float64), 0.0)
+    w = _omega(hh.size, T)
+    r = np.asarray(z) - model_cf(t, alpha, active, hh, T)
+    v = np.einsum("pjk,pk->pj", W, r)
+    E = np.exp(1j * w[None, None, :] * t[:, :, None])
+    dpsi_da = hh[None, None, :] * E
+    dpsi_dt = 1j * w[None, None, :] * a[:, :, None] * dpsi_da
+    nn = np.asarray(n, dtype=np.float64)[:, None]
+    g_t = -2.0 * nn * np.sum(np.real(np.conj(v)[:, None, :] * dpsi_dt), axis=2)
+    g_a = -2.0 * nn * np.sum(np.real(np.conj(v)[:, None, :] * dpsi_da), axis=2)
     return np.where(act, g_t, 0.0), np.where(act, g_a, 0.0)

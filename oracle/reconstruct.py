@@ -48,7 +48,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .model import sketched_gradient
+from .model import SIGMA_RIDGE, sketched_gradient, weighted_gradient, weighting_matrix
 
 _PIXEL_BLOCK = 1024
 
@@ -65,6 +65,7 @@ class Params:
     smooth_lambda: float = 0.5
     min_sep: float = 12.0
     regularize: bool = True
+    weighting: int = 0  # 0: W = I (SRT3D); 1: W = Sigma_theta^-1 (Eq. 6), pixelwise mode only
 
 
 def step_sizes(hh, n_max: float, k_max: int, T: int):
@@ -139,9 +140,21 @@ def init_matched_filter(z, n, hh, T: int, params: Params):
     return t, alpha, active, alpha0
 
 
-def gradient_step(z, n, t, alpha, active, hh, T: int, eta_t: float, eta_a: float):
-    """One Jacobi gradient step on n ||z - Psi||^2 (Eq. 8 data term, W = I)."""
-    g_t, g_a = sketched_gradient(z, n, t, alpha, active, hh, T)
+def gradient_step(z, n, t, alpha, active, hh, T: int, eta_t: float, eta_a: float, weighting: int = 0):
+    """One Jacobi gradient step on n ||z - Psi||^2_W (Eq. 8 data term).
+    W = I, or (weighting = 1) W = (Sigma_theta + ridge I)^-1 evaluated at the
+    current state and held fixed for the step (iteratively reweighted). Since
+    Sigma_theta >= alpha_0 I (the uniform background's share of the
+    covariance), ||W|| <= 1 / (alpha_0 + ridge): the W = I step sizes times
+    alpha_0 + ridge of the pixel's current state stay valid bounds."""
+    if weighting:
+        W = weighting_matrix(t, alpha, active, hh, T)
+        g_t, g_a = weighted_gradient(z, n, t, alpha, active, hh, T, W)
+        a0 = np.maximum(0.0, 1.0 - np.where(active, alpha, 0.0).sum(axis=1))
+        scale = (a0 + SIGMA_RIDGE)[:, None]
+        eta_t, eta_a = eta_t * scale, eta_a * scale
+    else:
+        g_t, g_a = sketched_gradient(z, n, t, alpha, active, hh, T)
     t_new = np.where(active, np.mod(t - eta_t * g_t, T), t)
     a_new = np.where(active, np.maximum(alpha - eta_a * g_a, 0.0), 0.0)
     a_new = _project_simplex_cap(a_new, active)
@@ -271,7 +284,7 @@ def iterate(z, n, t, alpha, active, hh, T: int, rows: int, cols: int, params: Pa
             eta_t: float, eta_a: float):
     """One SRT3D iteration: gradient step, then (if regularising) APSS depth
     projection and intensity smoothing/pruning on the post-gradient state."""
-    t1, a1 = gradient_step(z, n, t, alpha, active, hh, T, eta_t, eta_a)
+    t1, a1 = gradient_step(z, n, t, alpha, active, hh, T, eta_t, eta_a, params.weighting)
     if not params.regularize:
         act = active.copy()
         return t1, a1, act, 1.0 - a1.sum(axis=1)

@@ -427,3 +427,102 @@ def test_reconstruct_small_frame_improves_on_init():
     assert dae1 < dae0
     assert dae1 < 2.5
     assert np.all(al0 >= -1e-12) and np.all(al0 <= 1 + 1e-12)
+
+
+# ---------------------------------------------------------------- weighted loss (Eq. 5-6, W = Sigma^-1)
+
+def test_sigma_theta_is_the_covariance_of_sampled_photons():
+    # Eq. 5: n Cov(z) -> Sigma_theta. Draw photons from the discrete model
+    # (surface k with probability alpha_k at (t_k + tau) mod T, tau ~ h / H;
+    # uniform background otherwise) and compare the sample covariance of
+    # exp(i w_l x) with Sigma_theta.
+    T, m = 256, 6
+    h = synth.impulse_response(T, 3.0)
+    hh = oracle.h_hat(h, m)
+    t = np.array([[40.0, 171.0]])
+    a = np.array([[0.35, 0.25]])
+    act = np.ones((1, 2), bool)
+    rng = np.random.default_rng(11)
+    N = 400_000
+    comp = rng.choice(3, size=N, p=[a[0, 0], a[0, 1], 1 - a[0].sum()])
+    tau = rng.choice(T, size=N, p=h / h.sum())
+    x = np.where(comp == 0, (40 + tau) % T, np.where(comp == 1, (171 + tau) % T, rng.integers(0, T, size=N)))
+    v = np.exp(1j * 2 * np.pi * np.outer(x, np.arange(1, m + 1)) / T)
+    mu = v.mean(axis=0)
+    C = (v.T @ np.conj(v)) / N - np.outer(mu, np.conj(mu))
+    S = oracle.sigma_theta(t, a, act, hh, T)[0]
+    assert np.max(np.abs(C - S)) <= 6.0 / np.sqrt(N)
+
+
+def test_sigma_theta_bounded_below_by_the_background_share():
+    T, m = 512, 8
+    hh = oracle.h_hat(synth.impulse_response(T, 2.0), m)
+    rng = np.random.default_rng(12)
+    t = rng.uniform(0, T, size=(50, 2))
+    a = rng.dirichlet([1, 1, 1], size=50)[:, :2]
+    act = rng.uniform(size=(50, 2)) < 0.8
+    S = oracle.sigma_theta(t, a, act, hh, T)
+    a0 = 1 - np.where(act, a, 0).sum(axis=1)
+    lam = np.linalg.eigvalsh(S)
+    assert np.all(lam[:, 0] >= a0 - 1e-12)
+    np.testing.assert_allclose(S, np.conj(np.transpose(S, (0, 2, 1))), atol=1e-15)
+
+
+def test_weighted_gradient_of_pure_background_is_scaled_identity_gradient():
+    T, m = 128, 5
+    hh = oracle.h_hat(synth.impulse_response(T, 2.0), m)
+    rng = np.random.default_rng(13)
+    z = rng.normal(size=(3, m)) + 1j * rng.normal(size=(3, m))
+    t = rng.uniform(0, T, size=(3, 1))
+    a = np.zeros((3, 1))
+    act = np.zeros((3, 1), bool)
+    W = oracle.weighting_matrix(t, a, act, hh, T)
+    np.testing.assert_allclose(W, np.broadcast_to(np.eye(m) / (1 + oracle.SIGMA_RIDGE), W.shape), atol=1e-15)
+
+
+def test_weighted_gradient_matches_finite_differences():
+    T, m = 256, 6
+    hh = oracle.h_hat(synth.impulse_response(T, 3.0), m)
+    rng = np.random.default_rng(14)
+    P, K = 4, 2
+    t = rng.uniform(20, T - 20, size=(P, K))
+    a = rng.uniform(0.1, 0.4, size=(P, K))
+    act = np.ones((P, K), bool)
+    z = oracle.model_cf(t + rng.normal(size=(P, K)), a * 1.1, act, hh, T) + 0.01 * rng.normal(size=(P, m))
+    n = np.array([50, 200, 1000, 7])
+    W = oracle.weighting_matrix(t, a, act, hh, T)
+    g_t, g_a = oracle.weighted_gradient(z, n, t, a, act, hh, T, W)
+    eps = 1e-6
+    for k in range(K):
+        dt = np.zeros((P, K))
+        dt[:, k] = eps
+        fd = (oracle.weighted_loss(z, n, t + dt, a, act, hh, T, W) -
+              oracle.weighted_loss(z, n, t - dt, a, act, hh, T, W)) / (2 * eps)
+        np.testing.assert_allclose(g_t[:, k], fd, rtol=1e-6, atol=1e-6)
+        fd = (oracle.weighted_loss(z, n, t, a + dt, act, hh, T, W) -
+              oracle.weighted_loss(z, n, t, a - dt, act, hh, T, W)) / (2 * eps)
+        np.testing.assert_allclose(g_a[:, k], fd, rtol=1e-6, atol=1e-6)
+
+
+def test_weighted_step_decreases_the_weighted_loss():
+    # the step sizes (W = I bounds times alpha_0 + ridge) are descent steps
+    # for the loss with W fixed at the start of the step
+    T, m = 512, 8
+    h = synth.impulse_response(T, 3.0)
+    hh = oracle.h_hat(h, m)
+    rng = np.random.default_rng(15)
+    P, K = 64, 2
+    t_true = rng.uniform(0, T, size=(P, K))
+    a_true = rng.uniform(0.1, 0.4, size=(P, K))
+    act = np.ones((P, K), bool)
+    z = oracle.model_cf(t_true, a_true, act, hh, T)
+    n = rng.integers(10, 2000, size=P)
+    t = t_true + rng.normal(scale=2.0, size=(P, K))
+    a = a_true * rng.uniform(0.8, 1.2, size=(P, K))
+    eta_t, eta_a = oracle.step_sizes(hh, n.max(), K, T)
+    W = oracle.weighting_matrix(t, a, act, hh, T)
+    L0 = oracle.weighted_loss(z, n, t, a, act, hh, T, W)
+    t1, a1 = oracle.gradient_step(z, n, t, a, act, hh, T, eta_t, eta_a, weighting=1)
+    L1 = oracle.weighted_loss(z, n, t1, a1, act, hh, T, W)
+    assert np.all(L1 <= L0 + 1e-12)
+    assert np.mean(L1 < L0) > 0.9
