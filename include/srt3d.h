@@ -94,6 +94,10 @@ typedef struct srt3d_params {
   float prune_alpha;   /* a point with alpha below this is removed           */
   float smooth_lambda; /* intensity smoothing weight in [0, 1]               */
   float min_sep;       /* init: least circular separation of 2 surfaces, bins */
+  int32_t weighting;   /* data-term weight W of Eq. 6: 0 = identity (SRT3D);
+                          1 = (Sigma_theta + 1e-3 I)^-1, Sigma_theta of Eq. 5 at
+                          the current state, re-evaluated every iteration;
+                          1 requires regularize = 0 (pixelwise estimate)      */
 } srt3d_params;
 
 /* Create a context on CUDA device `device`. hbm_budget_bytes bounds the device

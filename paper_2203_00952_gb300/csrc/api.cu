@@ -88,6 +88,9 @@ srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint3
       !(prm->min_sep >= 0.f))
     return set_error(ctx, SRT3D_EINVAL, "invalid float parameter");
   if (prm->iters > 100000) return set_error(ctx, SRT3D_EINVAL, "iters too large");
+  if (prm->weighting != 0 && prm->weighting != 1) return set_error(ctx, SRT3D_EINVAL, "weighting must be 0 or 1");
+  if (prm->weighting && prm->regularize)
+    return set_error(ctx, SRT3D_EINVAL, "the weighted loss is available in pixelwise mode (regularize = 0)");
   return SRT3D_OK;
 }
 

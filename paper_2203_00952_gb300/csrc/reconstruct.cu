@@ -266,8 +266,146 @@ __device__ __forceinline__ void grad_pixel(const float2* __restrict__ zp, uint32
   }
 }
 
-// Pixelwise iteration (regularize = 0): the gradient step is the new state.
+// Ridge added to Sigma_theta before inverting it (Sigma_theta is singular for
+// a noise-free point mass).
+constexpr float kSigmaRidge = 1e-3f;
+
+// Solves A x = y and A u = g for the Hermitian positive definite Toeplitz
+// matrix A_jk = c_{j-k} (c_0 real, c_{-d} = conj(c_d)), size m, by the Levinson
+// recursion (O(m^2) operations, O(m) storage): the forward vector f solves
+// A_n f = e_1, the backward vector is its conjugate reversal, and each order
+// n -> n + 1 updates f, x and u with the new row's residuals.
+__device__ __forceinline__ void levinson2(float c0, const float2* c, uint32_t m, const float2* y, const float2* g,
+                                          float2* f, float2* x, float2* u) {
+  const float inv0 = 1.f / c0;
+  f[0] = make_float2(inv0, 0.f);
+  x[0] = make_float2(y[0].x * inv0, y[0].y * inv0);
+  u[0] = make_float2(g[0].x * inv0, g[0].y * inv0);
+  for (uint32_t n = 1; n < m; ++n) {
+    // residuals of [f; 0], [x; 0], [u; 0] in the new row: sum_k c_{n-k} v_k
+    float2 ef = make_float2(0.f, 0.f), ex = ef, eu = ef;
+    for (uint32_t k = 0; k < n; ++k) {
+      const float2 cv = c[n - k - 1];  // c_{n-k}
+      ef = make_float2(ef.x + cv.x * f[k].x - cv.y * f[k].y, ef.y + cv.x * f[k].y + cv.y * f[k].x);
+      ex = make_float2(ex.x + cv.x * x[k].x - cv.y * x[k].y, ex.y + cv.x * x[k].y + cv.y * x[k].x);
+      eu = make_float2(eu.x + cv.x * u[k].x - cv.y * u[k].y, eu.y + cv.x * u[k].y + cv.y * u[k].x);
+    }
+    const float invD = 1.f / (1.f - (ef.x * ef.x + ef.y * ef.y));
+    // f' = ([f; 0] - ef [0; b]) / D with b_j = conj(f_{n-1-j}), in place
+    // over the pairs (k, n - k)
+    f[n] = make_float2(0.f, 0.f);
+    for (uint32_t k = 0, j = n; k <= j; ++k, --j) {
+      const float2 fk = f[k], fj = f[j];
+      const float2 ck = make_float2(fj.x, -fj.y), cj = make_float2(fk.x, -fk.y);  // conj(f_{n-k}), conj(f_{n-j})
+      f[k] = make_float2((fk.x - (ef.x * ck.x - ef.y * ck.y)) * invD, (fk.y - (ef.x * ck.y + ef.y * ck.x)) * invD);
+      if (j != k)
+        f[j] = make_float2((fj.x - (ef.x * cj.x - ef.y * cj.y)) * invD, (fj.y - (ef.x * cj.y + ef.y * cj.x)) * invD);
+    }
+    // x' = [x; 0] + (y_n - ex) b', b'_j = conj(f'_{n-j}); the same for u
+    const float2 mx = make_float2(y[n].x - ex.x, y[n].y - ex.y), mu = make_float2(g[n].x - eu.x, g[n].y - eu.y);
+    x[n] = make_float2(0.f, 0.f);
+    u[n] = make_float2(0.f, 0.f);
+    for (uint32_t j = 0; j <= n; ++j) {
+      const float2 b = make_float2(f[n - j].x, -f[n - j].y);
+      x[j] = make_float2(x[j].x + mx.x * b.x - mx.y * b.y, x[j].y + mx.x * b.y + mx.y * b.x);
+      u[j] = make_float2(u[j].x + mu.x * b.x - mu.y * b.y, u[j].y + mu.x * b.y + mu.y * b.x);
+    }
+  }
+}
+
+// The gradient step of pixelwise mode with W = (Sigma_theta + ridge I)^-1
+// (Eq. 6): Sigma_theta = A - psi psi^H with A_jk = Psi(w_j - w_k) (Toeplitz,
+// Psi(0) = 1) and psi_l = Psi_l the model at the current state, so v = W r
+// comes from the Levinson solves A x = r, A u = psi and Sherman-Morrison,
+// v = x + u (psi^H x) / (1 - psi^H u). The gradient is the W = I one with r
+// replaced by v; the step sizes are the W = I bounds times alpha_0 + ridge
+// (||W|| <= 1 / (alpha_0 + ridge) since Sigma_theta >= alpha_0 I).
 template <int K>
+__device__ __forceinline__ void grad_pixel_w(const float2* __restrict__ zp, uint32_t cnt, uint32_t T, uint32_t m,
+                                             const float2* s_hh, float eta_t, float eta_a, float (&t)[K],
+                                             float (&a)[K], const bool (&act)[K]) {
+  const float Tf = float(T);
+  float2 e1[K], E[K];
+  float aa[K];
+  float a0 = 1.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float sn, cs;
+    sincospif(2.f * t[k] / Tf, &sn, &cs);
+    e1[k] = make_float2(cs, sn);
+    E[k] = e1[k];
+    aa[k] = act[k] ? a[k] : 0.f;
+    a0 -= aa[k];
+  }
+  float2 psi[kMaxM], r[kMaxM], f[kMaxM], x[kMaxM], u[kMaxM];
+  for (uint32_t l = 0; l < m; ++l) {
+    const float2 hv = s_hh[l];
+    float2 ps = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 q = cmul(hv, E[k]);
+      ps.x = fmaf(aa[k], q.x, ps.x);
+      ps.y = fmaf(aa[k], q.y, ps.y);
+      E[k] = cmul(E[k], e1[k]);
+    }
+    psi[l] = ps;
+    const float2 zl = zp[l];
+    r[l] = make_float2(zl.x - ps.x, zl.y - ps.y);
+  }
+  levinson2(1.f + kSigmaRidge, psi, m, r, psi, f, x, u);
+  float2 px = make_float2(0.f, 0.f);
+  float pu = 0.f;
+  for (uint32_t l = 0; l < m; ++l) {
+    px = make_float2(px.x + psi[l].x * x[l].x + psi[l].y * x[l].y, px.y + psi[l].x * x[l].y - psi[l].y * x[l].x);
+    pu += psi[l].x * u[l].x + psi[l].y * u[l].y;
+  }
+  const float inv = 1.f / (1.f - pu);
+  const float2 sm = make_float2(px.x * inv, px.y * inv);
+  float gt[K], ga[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    gt[k] = ga[k] = 0.f;
+    E[k] = e1[k];
+  }
+  const float wstep = 6.283185307179586f / Tf;
+  for (uint32_t l = 0; l < m; ++l) {
+    const float2 v = make_float2(x[l].x + u[l].x * sm.x - u[l].y * sm.y, x[l].y + u[l].x * sm.y + u[l].y * sm.x);
+    const float2 hv = s_hh[l];
+    const float w = wstep * float(l + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float2 q = cmul(hv, E[k]);
+      ga[k] += v.x * q.x + v.y * q.y;
+      gt[k] += w * a[k] * (v.y * q.x - v.x * q.y);
+      E[k] = cmul(E[k], e1[k]);
+    }
+  }
+  const float scale = fmaxf(a0, 0.f) + kSigmaRidge;
+  const float nn = -2.f * float(cnt);
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (act[k]) {
+      float xk = t[k] - eta_t * scale * (nn * gt[k]);
+      xk -= floorf(xk / Tf) * Tf;
+      if (xk >= Tf) xk -= Tf;
+      if (xk < 0.f) xk += Tf;
+      t[k] = xk;
+      a[k] = fmaxf(a[k] - eta_a * scale * (nn * ga[k]), 0.f);
+    } else {
+      a[k] = 0.f;
+    }
+    sum += a[k];
+  }
+  if (sum > 1.f) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
+  }
+}
+
+// Pixelwise iteration (regularize = 0): the gradient step is the new state.
+// With `weighted`, W = (Sigma_theta + ridge I)^-1 instead of I.
+template <int K, bool WEIGHTED>
 __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, const uint32_t* __restrict__ n,
                                                  uint32_t P, uint32_t T, uint32_t m,
                                                  const float2* __restrict__ hh_g, const float* __restrict__ misc,
@@ -286,7 +424,12 @@ __global__ void __launch_bounds__(kBlock) k_grad(const float2* __restrict__ z, c
     a[k] = alpha[size_t(p) * K + k];
     act[k] = active[size_t(p) * K + k] != 0;
   }
-  grad_pixel<K>(z + size_t(p) * m, n[p], T, m, s_hh, misc[MISC_ETA_T] / nmax, misc[MISC_ETA_A] / nmax, t, a, act);
+  if (WEIGHTED)
+    grad_pixel_w<K>(z + size_t(p) * m, n[p], T, m, s_hh, misc[MISC_ETA_T] / nmax, misc[MISC_ETA_A] / nmax, t, a,
+                    act);
+  else
+    grad_pixel<K>(z + size_t(p) * m, n[p], T, m, s_hh, misc[MISC_ETA_T] / nmax, misc[MISC_ETA_A] / nmax, t, a,
+                  act);
   float s2 = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
@@ -1106,7 +1249,10 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     float* aout = from_scratch ? alpha : sc.a1;
     uint8_t* cout = from_scratch ? active : sc.act1;
     if (!prm.regularize) {
-      k_grad<K><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      if (prm.weighting)
+        k_grad<K, true><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      else
+        k_grad<K, false><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
     } else if (prm.radius == 1) {
       k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
                                                            aout, cout, alpha0);

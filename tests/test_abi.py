@@ -41,10 +41,11 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_params_struct_layout_matches_header():
-    # 5 x 32-bit integers followed by 6 floats, no padding
-    assert ctypes.sizeof(binding.srt3d_params) == 44
+    # 5 x 32-bit integers, 6 floats, one 32-bit integer, no padding
+    assert ctypes.sizeof(binding.srt3d_params) == 48
     assert binding.srt3d_params.apss_h.offset == 20
     assert binding.srt3d_params.min_sep.offset == 40
+    assert binding.srt3d_params.weighting.offset == 44
 
 
 def test_frame_struct_layout_matches_header():

@@ -33,7 +33,7 @@ def gpu_params(p: Params, init_mode, iters=None):
     return B.make_params(iters=p.iters if iters is None else iters, k_max=p.k_max, radius=p.radius,
                          init_mode=init_mode, regularize=int(p.regularize), apss_h=p.apss_h, d_max=p.d_max,
                          depth_scale=p.depth_scale, prune_alpha=p.prune_alpha, smooth_lambda=p.smooth_lambda,
-                         min_sep=p.min_sep)
+                         min_sep=p.min_sep, weighting=p.weighting)
 
 
 def sketch_frame(ctx, fr, m):
@@ -155,6 +155,47 @@ def multi_surface_inputs(ctx, K, seed, m=20, rows=24, cols=28):
     h32 = synth.impulse_response(spec.T, spec.sigma).astype(np.float32)
     hh = oracle.h_hat(h32.astype(np.float64), m)
     return fr, spec, z, n, to_complex(z), counts(n), h32, hh
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_weighted_pixelwise_iterations(ctx, K):
+    # W = (Sigma_theta + ridge I)^-1 (Eq. 6) in pixelwise mode: one step from a
+    # shared state, then 20 steps from the oracle's init
+    spec = synth.FrameSpec(rows=20, cols=24, T=1024, sigma=4.0, mean_photons=400.0, sbr=1.0, two_surface_frac=0.3)
+    m = 8
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, 90 + K, m)
+    p = oracle_params(iters=1, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma, regularize=False,
+                      weighting=1)
+    s0 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, iters=3)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=s0[:3], iters=1)
+    eta = oracle.step_sizes(hh, n_np.max(), K, spec.T)
+    r = oracle.iterate(z_np, n_np, s0[0], s0[1], s0[2], hh, spec.T, spec.rows, spec.cols, p, *eta)
+    compare_state(g, r, n_np, 1e-3, 1e-4, 0.0, f"one weighted step, K = {K}", spec.T)
+    p20 = oracle_params(iters=20, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma, regularize=False,
+                        weighting=1)
+    init = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p20)[:3]
+    g20 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p20, init=init)
+    r20 = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p20, init=init)
+    compare_state(g20, r20, n_np, DEPTH_TOL, INTENSITY_RTOL, 0.0, f"20 weighted steps, K = {K}", spec.T)
+    # the weighted estimate differs from the unweighted one
+    pu = oracle_params(iters=20, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma, regularize=False)
+    gu = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, pu, init=init)
+    assert np.max(np.abs(gu[0] - g20[0])) > 1e-3
+
+
+def test_weighted_loss_needs_pixelwise_mode(ctx):
+    T, m = 64, 4
+    z = torch.zeros(4, m, 2, device="cuda")
+    n = torch.zeros(4, dtype=torch.int32, device="cuda")
+    h = torch.ones(T, device="cuda")
+    d = torch.zeros(4, 1, device="cuda")
+    a = torch.zeros(4, 1, device="cuda")
+    act = torch.zeros(4, 1, dtype=torch.uint8, device="cuda")
+    a0 = torch.zeros(4, device="cuda")
+    for kw in (dict(weighting=1, regularize=1), dict(weighting=2, regularize=0)):
+        with pytest.raises(B.SRT3DError) as ei:
+            B.srt3d_reconstruct(ctx, z, n, 2, 2, T, m, h, B.make_params(**kw), d, a, act, a0)
+        assert ei.value.status == B.SRT3D_EINVAL
 
 
 @pytest.mark.parametrize("K", [3, 4])
