@@ -48,7 +48,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
-    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces"], default="all")
+    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces", "pixelwise"],
+                    default="all")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
@@ -244,6 +245,61 @@ def hist_section(B, ctx, dev, steps, flush):
     out["hbm_peak_gbs"] = hbm_peak
     out["peak_source"] = f"MEASURED_PEAKS.json ({peak_kind})"
     del hist, S, n
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------- pixelwise
+def pixelwise_section(B, ctx, dev, stamps, offsets, fr, spec, prm_main, steps, flush):
+    """Pixelwise sketched estimates on the 256x256 frame (regularize = 0,
+    K = 2, 30 steps): W = I (the SMLE comparison of Sec. 4) and W =
+    (Sigma_theta + ridge I)^-1 (Eq. 6); step time (sketch, finalize,
+    reconstruct; CUDA events, L2 evicted between steps) and the depth error
+    of the first surface against the synthetic truth."""
+    import numpy as np
+    import torch
+
+    from paper_2203_00952_gb300 import synth
+
+    P, T, m, K = spec.num_pixels, spec.T, WORKLOAD["m"], WORKLOAD["k_max"]
+    N = int(fr.offsets[-1])
+    S = torch.empty(P, m, 2, device=dev)
+    n = torch.empty(P, dtype=torch.int32, device=dev)
+    depth = torch.empty(P, K, device=dev)
+    alpha = torch.empty(P, K, device=dev)
+    active = torch.empty(P, K, dtype=torch.uint8, device=dev)
+    alpha0 = torch.empty(P, device=dev)
+    h = torch.from_numpy(synth.impulse_response(T, spec.sigma).astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "pixelwise_256x256_T4096_m10_K2_it30"}
+    for name, wgt in (("W_identity", 0), ("W_precision", 1)):
+        prm = B.make_params(iters=prm_main.iters, k_max=K, regularize=0, weighting=wgt, d_max=prm_main.d_max,
+                            min_sep=prm_main.min_sep)
+
+        def step():
+            B.srt3d_sketch_stream(ctx, stamps, offsets, T, m, 0, S, n, stream)
+            B.srt3d_finalize(ctx, S, n, m, S, stream)
+            B.srt3d_reconstruct(ctx, S, n, spec.rows, spec.cols, T, m, h, prm, depth, alpha, active, alpha0, stream)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        d = depth.cpu().numpy()
+        act = active.cpu().numpy().astype(bool)
+        err = np.abs(d[:, 0] - fr.truth.depth[:, 0])
+        err = np.minimum(err, T - err)
+        det = act[:, 0] & (err <= 3 * spec.sigma)
+        out[name] = {"ms_per_step": ms, "photons_per_s": N / (ms / 1e3), "dae_bins": float(err[det].mean()),
+                     "detections": float(det.mean())}
+    del S, n, depth, alpha, active, alpha0
     torch.cuda.empty_cache()
     return out
 
@@ -731,9 +787,11 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
     d2h = sum(o.nbytes for o in outs if o is not None)
 
-    hist = batch = surfaces = None
+    hist = batch = surfaces = pixelwise = None
     if args.only in ("all", "hist") and rank == 0:
         hist = hist_section(B, ctx, dev, args.hist_steps, flush)
+    if args.only in ("all", "pixelwise") and rank == 0:
+        pixelwise = pixelwise_section(B, ctx, dev, stamps, offsets, fr, spec, params, args.batch_steps, flush)
     if args.only == "all" and rank == 0:
         del stamps, offsets, S, z
         torch.cuda.empty_cache()
@@ -814,6 +872,7 @@ def gpu_arm(args):
         "hist_sketch": hist,
         "batch": batch,
         "surfaces": surfaces,
+        "pixelwise": pixelwise,
         "serving": serving,
     }
     print(json.dumps(out), flush=True)
