@@ -589,7 +589,7 @@ def mf_grid_spacing(T, m):
 
 
 def kernel_work(name, N, P, m, T, K, iters):
-    """Algorithmic work of one launch of kernel `name` (see DESIGN.md: per
+    """Algorithmic work of one launch of kernel `name` (per
     photon / pixel / point figures). Returns (bound, amount, unit)."""
     if name == "sketch_stream":
         # FP32 operations per photon: per harmonic two accumulations and, from
@@ -847,7 +847,7 @@ def gpu_arm(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded generator; Eq. 1 observation model, see DESIGN.md)",
+        "data": "synthetic (seeded generator of the Eq. 1 observation model: smooth depth map, Poisson counts, SBR, Gaussian pulse)",
         "config": {"workload": WORKLOAD_NAME, **{k: WORKLOAD[k] for k in ("rows", "cols", "T", "m", "iters",
                                                                           "k_max")},
                    "photons_per_frame": N, "frames_per_step_per_gpu": 1,
@@ -909,7 +909,7 @@ def reference_arm(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded generator; Eq. 1 observation model, see DESIGN.md)",
+        "data": "synthetic (seeded generator of the Eq. 1 observation model: smooth depth map, Poisson counts, SBR, Gaussian pulse)",
         "config": {"workload": WORKLOAD_NAME, **{k: WORKLOAD[k] for k in ("rows", "cols", "T", "m", "iters",
                                                                           "k_max")}},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": last["sample"]},
