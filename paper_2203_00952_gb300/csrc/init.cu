@@ -318,7 +318,7 @@ __device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict_
 // Also folds the frame's largest photon count n_max (zeroed by the prep
 // kernel) into misc[MISC_NMAX] for the iterations' step sizes.
 template <int K, int M>
-__global__ void __launch_bounds__(kBlock, 1) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
+__global__ void __launch_bounds__(kBlock, M <= 12 ? 4 : 1) k_init(const float2* __restrict__ z, const uint32_t* __restrict__ n,
                                                  uint32_t P, uint32_t T, uint32_t m,
                                                  const float2* __restrict__ table, uint32_t entries,
                                                  int two_level, uint32_t D, const float2* __restrict__ hh_g,
