@@ -236,7 +236,7 @@ __device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, ui
 }
 
 template <int M>
-__global__ void __launch_bounds__(kBlock, M <= 10 ? 5 : 1) k_sketch_stream(
+__global__ void __launch_bounds__(kBlock, M <= 10 ? 5 : (M <= 16 ? 3 : 2)) k_sketch_stream(
     const uint16_t* __restrict__ stamps, const uint32_t* __restrict__ offsets, uint32_t num_stamps,
     uint32_t P, uint32_t T, uint32_t m, int glog2, int accumulate, const float2* __restrict__ table,
     uint32_t tab_entries, int two_level, float2* __restrict__ S, uint32_t* __restrict__ n,
