@@ -15,9 +15,10 @@
 //             Gross 2007) and projection along the line of sight; intensity
 //             smoothing, pruning, alpha_0 = 1 - sum alpha
 //   k_grad    the gradient step alone (pixelwise mode, no spatial prior)
-// The iteration state lives in the caller's depth/alpha/active buffers; the
-// post-gradient state and the normals live in shared memory; hhat and the
-// step sizes live in a scratch block.
+// The iteration state lives in the caller's depth/alpha/active buffers (and,
+// in the persistent kernel, in registers between iterations); the
+// post-gradient state and the normals live in shared memory; hhat, the step
+// sizes and the persistent kernel's exchange buffers live in a scratch block.
 #include <cfloat>
 #include <cmath>
 #include <cstdlib>
@@ -36,7 +37,7 @@ constexpr int kMaxM = 32;
 struct Scratch {
   float* t1;
   float* a1;
-  float4* nrm;
+  float* xch;  // exchange buffer 0 of the persistent kernel: t, alpha [P][K] f32, active [P][K] u8
   uint8_t* act1;
   float2* hh;
   float* misc;
@@ -48,8 +49,8 @@ Scratch carve(void* base, uint32_t P, uint32_t K) {
   char* p = static_cast<char*>(base);
   Scratch s;
   const size_t pk = size_t(P) * K;
-  s.nrm = reinterpret_cast<float4*>(p);
-  p += align256(pk * sizeof(float4));
+  s.xch = reinterpret_cast<float*>(p);
+  p += align256(pk * 16);
   s.t1 = reinterpret_cast<float*>(p);
   p += align256(pk * sizeof(float));
   s.a1 = reinterpret_cast<float*>(p);
@@ -675,16 +676,17 @@ __device__ __forceinline__ void load_state(const float* depth, const float* alph
 
 // Gradient step of region pixel i (at array row rr, column cc; `in` = inside
 // the array, else inactive) from the state (t, a, act); the post-step state
-// goes to shared memory. The pixel's sketch comes from s_z / s_nn when given.
+// goes to shared memory and stays in (t, a, act). The pixel's sketch comes
+// from s_z / s_nn (entry zi) when given, else from global memory.
 template <int K, int R>
 __device__ __forceinline__ void grad_to_smem(TileSmem<K, R>& sm, const Stencil& st, int i, int rr, int cc, bool in,
                                              float (&t)[K], float (&a)[K], bool (&act)[K],
                                              const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T,
                                              uint32_t m, float eta_t, float eta_a, const float2* s_z,
-                                             const uint32_t* s_nn) {
+                                             const uint32_t* s_nn, int zi = 0) {
   if (in) {
     if (s_z)
-      grad_pixel<K>(s_z + size_t(i) * m, s_nn[i], T, m, sm.hh, eta_t, eta_a, t, a, act);
+      grad_pixel<K>(s_z + size_t(zi) * m, s_nn[zi], T, m, sm.hh, eta_t, eta_a, t, a, act);
     else {
       const size_t p = size_t(rr) * st.cols + size_t(cc);
       grad_pixel<K>(z + p * m, n[p], T, m, sm.hh, eta_t, eta_a, t, a, act);
@@ -697,6 +699,19 @@ __device__ __forceinline__ void grad_to_smem(TileSmem<K, R>& sm, const Stencil& 
       act[k] = false;
     }
   }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    sm.t[i][k] = t[k];
+    sm.a[i][k] = a[k];
+    sm.act[i][k] = act[k] ? 1 : 0;
+    sm.tm[i][k] = act[k] ? t[k] : kMaskedDepth;
+  }
+}
+
+// A region pixel's post-gradient state into shared memory.
+template <int K, int R>
+__device__ __forceinline__ void put_state(TileSmem<K, R>& sm, int i, const float (&t)[K], const float (&a)[K],
+                                          const bool (&act)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     sm.t[i][k] = t[k];
@@ -795,7 +810,7 @@ __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, in
 template <int K, int R>
 __device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, int r0, int c0, int th, float* depth,
                                        float* alpha, uint8_t* active, float* alpha0, float (&tout)[K],
-                                       float (&aout)[K], bool (&aact)[K]) {
+                                       float (&aout)[K], bool (&aact)[K], bool store = true) {
   constexpr int H = TileSmem<K, R>::H, RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
   const int tid = threadIdx.x;
   if (tid >= kTW * th) return false;
@@ -869,14 +884,16 @@ __device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, in
 #pragma unroll
     for (int k = 0; k < K; ++k) sum += aout[k];
   }
-  const size_t p = size_t(rr) * st.cols + size_t(cc);
+  if (store) {
+    const size_t p = size_t(rr) * st.cols + size_t(cc);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    depth[p * K + k] = tout[k];
-    alpha[p * K + k] = aout[k];
-    active[p * K + k] = aact[k] ? 1 : 0;
+    for (int k = 0; k < K; ++k) {
+      depth[p * K + k] = tout[k];
+      alpha[p * K + k] = aout[k];
+      active[p * K + k] = aact[k] ? 1 : 0;
+    }
+    alpha0[p] = 1.f - sum;
   }
-  alpha0[p] = 1.f - sum;
   return true;
 }
 
@@ -987,41 +1004,50 @@ __device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32
   return *s_abort == 0;
 }
 
-// All iterations in one cooperative launch, one CTA per tile: the tile's
-// region of sketches and counts is loaded into shared memory once; between
-// iterations the state goes through global memory (ping-pong buffers) and a
-// grid barrier. The gradient step is pixelwise, so a CTA computes the next
-// iteration's step for its own tile from the state it just produced between
-// arriving at the barrier and waiting on it; after the wait it only steps the
-// halo pixels, whose state its neighbours wrote. Tiles are kTW x th (th <=
-// kTH, chosen by the launcher to balance the tiles over the SMs).
+// Post-gradient state of every point, exchanged between the CTAs of the
+// persistent kernel (structure of arrays, [P][K]).
+struct XBuf {
+  float* t;
+  float* a;
+  uint8_t* c;
+};
+
+// All iterations in one cooperative launch, one CTA per kTW x th tile (th <=
+// kTH, chosen by the launcher to balance the tiles over the SMs); the tile's
+// sketches and counts are loaded into shared memory once. Per iteration a
+// CTA takes the gradient step of its own pixels (pixelwise, from the state it
+// produced last iteration or the initial state), publishes the post-gradient
+// state to one of two exchange buffers, passes a grid barrier, reads its
+// halo's post-gradient state from that buffer, and runs the normals and the
+// projection stages. The buffers alternate by iteration: a CTA rewrites
+// buffer (it + 1) & 1 only after the barrier of iteration it, which every CTA
+// reaches only after reading its halo of iteration it - 1 from that buffer.
+// The final state goes to the caller's buffers after the last iteration.
 template <int K, int R>
 __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
-    float* alpha0, float* alt_d, float* alt_a, uint8_t* alt_c, uint32_t iters, uint32_t tiles_x, uint32_t th_u,
-    uint32_t* __restrict__ flags) {
+    float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags) {
   using S = TileSmem<K, R>;
   constexpr int H = S::H, RW = S::RW;
-  const int th = int(th_u), RH = th + 2 * H, halo = RH * RW - kTW * th;
   constexpr int NT = iter_threads<R>();
+  const int th = int(th_u), RH = th + 2 * H, halo = RH * RW - kTW * th, npx = kTW * th;
   __shared__ S sm;
   __shared__ int s_abort;
-  extern __shared__ float2 s_z[];  // [RH * RW][m] sketches, then [RH * RW] counts
-  uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(S::RH) * RW * m);
+  extern __shared__ float2 s_z[];  // [kTW * kTH][m] sketches of the tile's pixels, then [kTW * kTH] counts
+  uint32_t* s_nn = reinterpret_cast<uint32_t*>(s_z + size_t(kTW) * kTH * m);
   const int tid = threadIdx.x;
   const uint32_t tile_x = blockIdx.x % tiles_x, tile_y = blockIdx.x / tiles_x;
   const int r0 = int(tile_y) * th, c0 = int(tile_x) * kTW;
-  for (uint32_t i = tid; i < uint32_t(RH * RW) * m; i += NT) {
+  for (uint32_t i = tid; i < uint32_t(npx) * m; i += NT) {
     const uint32_t q = i / m, l = i - q * m;
-    const int rr = r0 - H + int(q) / RW, cc = c0 - H + int(q) % RW;
-    const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
+    const int rr = r0 + int(q) / kTW, cc = c0 + int(q) % kTW;
+    const bool in = rr < int(st.rows) && cc < int(st.cols);
     s_z[i] = in ? z[(size_t(rr) * st.cols + size_t(cc)) * m + l] : make_float2(0.f, 0.f);
   }
-  for (uint32_t q = tid; q < uint32_t(RH * RW); q += NT) {
-    const int rr = r0 - H + int(q) / RW, cc = c0 - H + int(q) % RW;
-    const bool in = rr >= 0 && rr < int(st.rows) && cc >= 0 && cc < int(st.cols);
-    s_nn[q] = in ? n[size_t(rr) * st.cols + size_t(cc)] : 0u;
+  for (int q = tid; q < npx; q += NT) {
+    const int rr = r0 + q / kTW, cc = c0 + q % kTW;
+    s_nn[q] = rr < int(st.rows) && cc < int(st.cols) ? n[size_t(rr) * st.cols + size_t(cc)] : 0u;
   }
   if (tid < int(m)) sm.hh[tid] = hh_g[tid];
   if (tid == 0) s_abort = 0;
@@ -1029,39 +1055,67 @@ __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_pers
   const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
   unsigned* bar = reinterpret_cast<unsigned*>(misc) + MISC_BAR;
-  float tout[K], aout[K];
-  bool aact[K];
+  // the thread's own pixel (tid < npx) and its state between iterations
+  const int ty = tid / kTW, tx = tid % kTW;
+  const int rr = r0 + ty, cc = c0 + tx;
+  const bool mine = tid < npx;
+  const bool in = mine && rr < int(st.rows) && cc < int(st.cols);
+  const size_t p = in ? size_t(rr) * st.cols + size_t(cc) : 0;
+  float t[K], a[K];
+  bool act[K];
+  if (in) load_state<K>(depth, alpha, active, p, t, a, act);
   for (uint32_t it = 0; it < iters; ++it) {
-    const bool from_alt = ((iters - it) & 1u) != 0;  // the last iteration writes the caller's buffers
-    const float* d_in = from_alt ? alt_d : depth;
-    const float* a_in = from_alt ? alt_a : alpha;
-    const uint8_t* c_in = from_alt ? alt_c : active;
-    float* d_out = from_alt ? depth : alt_d;
-    float* a_out = from_alt ? alpha : alt_a;
-    uint8_t* c_out = from_alt ? active : alt_c;
-    // 1) gradient step: the whole region at the first iteration, else the
-    // halo (the tile's own pixels were stepped before the last barrier wait)
-    if (it == 0) {
-      for (int i = tid; i < RH * RW; i += NT)
-        stage1_pixel<K, R>(sm, st, i, r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z, s_nn);
-    } else {
-      for (int j = tid; j < halo; j += NT)
-        stage1_pixel<K, R>(sm, st, halo_index<R>(j, th), r0, c0, z, n, T, m, eta_t, eta_a, d_in, a_in, c_in, s_z,
-                           s_nn);
+    const XBuf xb = (it & 1u) ? x1 : x0;
+    // 1) gradient step of the own pixel, published for the neighbours
+    if (mine) {
+      grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z,
+                         s_nn, tid);
+      if (in) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          xb.t[p * K + k] = t[k];
+          xb.a[p * K + k] = a[k];
+          xb.c[p * K + k] = act[k] ? 1 : 0;
+        }
+      }
+    }
+    grid_arrive(bar);
+    if (!grid_wait(bar, (it + 1u) * gridDim.x, flags, &s_abort)) break;
+    // 2) the halo's post-gradient state
+    for (int j = tid; j < halo; j += NT) {
+      const int i = halo_index<R>(j, th);
+      const int hr = r0 - H + i / RW, hc = c0 - H + i % RW;
+      float ht[K], ha[K];
+      bool hact[K];
+      if (hr >= 0 && hr < int(st.rows) && hc >= 0 && hc < int(st.cols)) {
+        load_state<K>(xb.t, xb.a, xb.c, size_t(hr) * st.cols + size_t(hc), ht, ha, hact);
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          ht[k] = 0.f;
+          ha[k] = 0.f;
+          hact[k] = false;
+        }
+      }
+      put_state<K, R>(sm, i, ht, ha, hact);
     }
     __syncthreads();
-    // 2) normals, 3) projection, smoothing and pruning
+    // 3) normals, 4) projection, smoothing and pruning
     stage2<K, R>(sm, st, th);
     __syncthreads();
-    const bool own = stage3<K, R>(sm, st, r0, c0, th, d_out, a_out, c_out, alpha0, tout, aout, aact);
-    if (it + 1 == iters) break;
-    grid_arrive(bar);
-    if (tid < kTW * th) {
-      const int ty = tid / kTW, tx = tid % kTW;
-      grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), r0 + ty, c0 + tx, own, tout, aout, aact, z, n, T, m,
-                         eta_t, eta_a, s_z, s_nn);
+    float tout[K], aout[K];
+    bool aact[K];
+    const bool own = stage3<K, R>(sm, st, r0, c0, th, depth, alpha, active, alpha0, tout, aout, aact,
+                                  it + 1u == iters);
+    if (own) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        t[k] = tout[k];
+        a[k] = aout[k];
+        act[k] = aact[k];
+      }
     }
-    if (!grid_wait(bar, (it + 1u) * gridDim.x, flags, &s_abort)) break;
+    __syncthreads();  // the next gradient step rewrites the tile's shared state
   }
 }
 
@@ -1105,9 +1159,9 @@ __global__ void k_alpha0(uint32_t P, const float* __restrict__ alpha, const uint
 
 // Tile height for the persistent kernel: the th in [4, kTH] whose tiles all
 // fit on the device at once (bps CTAs per SM) and minimise the work of the
-// busiest SM, ceil(tiles / SMs) x the per-tile work (pixels of the gradient
-// region + normals region + 2 x tile, the projection weighing double). 0 if
-// no th fits.
+// busiest SM, ceil(tiles / SMs) x the per-tile work (the tile's gradient
+// steps + the normals region + 2 x tile for the projection, + the halo
+// loads). 0 if no th fits.
 template <int R>
 uint32_t persistent_tile_height(uint32_t rows, uint32_t cols, int num_sms, int bps) {
   constexpr int H = 2 * R;
@@ -1117,8 +1171,8 @@ uint32_t persistent_tile_height(uint32_t rows, uint32_t cols, int num_sms, int b
   for (uint32_t th = kTH; th >= 4; --th) {
     const uint64_t ntiles = tiles_x * ((rows + th - 1) / th);
     if (ntiles > uint64_t(num_sms) * uint64_t(bps)) continue;
-    const uint64_t per_tile = uint64_t(th + 2 * H) * (kTW + 2 * H) + uint64_t(th + 2 * R) * (kTW + 2 * R) +
-                              2ull * kTW * th;
+    const uint64_t halo = uint64_t(th + 2 * H) * (kTW + 2 * H) - uint64_t(kTW) * th;
+    const uint64_t per_tile = uint64_t(kTW) * th + uint64_t(th + 2 * R) * (kTW + 2 * R) + 2ull * kTW * th + halo / 4;
     const uint64_t cost = (ntiles + num_sms - 1) / num_sms * per_tile;
     if (cost < best_cost) {
       best_cost = cost;
@@ -1139,9 +1193,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
     // the caller launches per iteration
     return SRT3D_EAGAIN;
   } else {
-  constexpr int H = 2 * R;
-  constexpr int RW = kTW + 2 * H, RH = kTH + 2 * H;
-  const size_t zsmem = size_t(RH) * RW * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
+  const size_t zsmem = size_t(kTW) * kTH * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
   auto fn = k_iter_persistent<K, R>;
   cudaFuncAttributes fa;
   SRT3D_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, fn));
@@ -1154,16 +1206,20 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   if (th == 0) return SRT3D_EAGAIN;
   const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
   const uint32_t ntiles = tiles_x * ((st.rows + th - 1) / th);
+  // exchange buffers: the scratch block's spare region and its alternate state
+  const size_t pk = size_t(st.rows) * st.cols * K;
+  XBuf x0{sc.xch, sc.xch + pk, reinterpret_cast<uint8_t*>(sc.xch + 2 * pk)};
+  XBuf x1{sc.t1, sc.a1, sc.act1};
   Stencil stv = st;
   const float2* zz = z;
   const uint32_t* nn = n;
   uint32_t TT = T, mm = m, it = iters, tx = tiles_x, thv = th;
   const float2* hh = sc.hh;
   float* misc = sc.misc;
-  float *d = depth, *a = alpha, *a0 = alpha0, *ad = sc.t1, *aa = sc.a1;
-  uint8_t *c = active, *ac = sc.act1;
+  float *d = depth, *a = alpha, *a0 = alpha0;
+  uint8_t* c = active;
   uint32_t* flags = ctx->d_flags;
-  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &ad, &aa, &ac, &it, &tx, &thv, &flags};
+  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &x0, &x1, &it, &tx, &thv, &flags};
   const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
   SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles), dim3(iter_threads<R>()),
                                                   args, zsmem, stream));
@@ -1211,15 +1267,6 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   st.lambda = prm.smooth_lambda;
   st.prune_alpha = prm.prune_alpha;
   const dim3 tiles((cols + kTW - 1) / kTW, (rows + kTH - 1) / kTH);
-  // Ping-pong between the caller's state and the scratch copy (t1, a1,
-  // act1): with an odd count the state is first copied to scratch, so that
-  // the last iteration always writes the caller's buffers.
-  const size_t pk = size_t(P) * K;
-  if (prm.regularize && (prm.iters & 1u)) {
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
-  }
   // All iterations in one cooperative launch when every tile's CTA fits on
   // the device at once (SRT3D_ITER_PERSISTENT=0 forces one launch per iteration).
   if (prm.regularize && prm.iters > 0) {
@@ -1238,6 +1285,15 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
                                            stream);
     }
     if (pst != SRT3D_EAGAIN) return pst;  // launched (or failed)
+  }
+  // One launch per iteration: ping-pong between the caller's state and the
+  // scratch copy (t1, a1, act1); with an odd count the state is first copied
+  // to scratch, so that the last iteration writes the caller's buffers.
+  const size_t pk = size_t(P) * K;
+  if (prm.regularize && (prm.iters & 1u)) {
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
   }
   for (uint32_t it = 0; it < prm.iters; ++it) {
     const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);
@@ -1343,7 +1399,7 @@ srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
   (void)m;
   const size_t pk = size_t(P) * k_max;
-  return align256(pk * sizeof(float4)) + 2 * align256(pk * sizeof(float)) + align256(pk) +
+  return align256(pk * 16) + 2 * align256(pk * sizeof(float)) + align256(pk) +
          align256(kMaxM * sizeof(float2)) + align256(MISC_COUNT * sizeof(float));
 }
 
