@@ -628,6 +628,14 @@ __host__ __device__ constexpr int iter_threads() {
   return (((kTW + 4 * R) * (kTH + 4 * R) + 31) / 32) * 32;
 }
 
+// Threads of the persistent kernel: the halo is loaded, not computed, so a
+// CTA needs one thread per pixel of the normals region (tile + R halo) at
+// most; at radius 1 that is 288 (16x14 tiles), which lets 3 CTAs share an SM.
+template <int R>
+__host__ __device__ constexpr int persist_threads() {
+  return R == 1 ? 288 : iter_threads<R>();
+}
+
 // Shared memory of one tile: the post-gradient state of the region (tile +
 // 2R halo) with a masked depth copy, and the normals of the tile + R halo
 // (for K = 2 held as component pairs of the two points in the same storage).
@@ -737,12 +745,11 @@ __device__ __forceinline__ void stage1_pixel(TileSmem<K, R>& sm, const Stencil& 
   grad_to_smem<K, R>(sm, st, i, rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z, s_nn);
 }
 
-// Stage 2: normals of the tile (th rows) plus an R halo.
-template <int K, int R>
+// Stage 2: normals of the tile (th rows) plus an R halo, NT threads.
+template <int K, int R, int NT>
 __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, int th) {
   constexpr int RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
   const int NH = th + 2 * R;
-  constexpr int NT = iter_threads<R>();
   const int tid = threadIdx.x;
   if constexpr (K == 2) {
     float2* s_nx = sm.nx();
@@ -919,7 +926,7 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
                        nullptr);
   __syncthreads();
   // 2) normals on the tile plus an R halo
-  stage2<K, R>(sm, st, kTH);
+  stage2<K, R, NT>(sm, st, kTH);
   __syncthreads();
   // 3) sphere projection, smoothing and pruning on the tile
   float tout[K], aout[K];
@@ -1024,13 +1031,13 @@ struct XBuf {
 // reaches only after reading its halo of iteration it - 1 from that buffer.
 // The final state goes to the caller's buffers after the last iteration.
 template <int K, int R>
-__global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_persistent(
+__global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
     float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags) {
   using S = TileSmem<K, R>;
   constexpr int H = S::H, RW = S::RW;
-  constexpr int NT = iter_threads<R>();
+  constexpr int NT = persist_threads<R>();
   const int th = int(th_u), RH = th + 2 * H, halo = RH * RW - kTW * th, npx = kTW * th;
   __shared__ S sm;
   __shared__ int s_abort;
@@ -1101,7 +1108,7 @@ __global__ void __launch_bounds__(iter_threads<R>(), R == 1 ? 2 : 1) k_iter_pers
     }
     __syncthreads();
     // 3) normals, 4) projection, smoothing and pruning
-    stage2<K, R>(sm, st, th);
+    stage2<K, R, NT>(sm, st, th);
     __syncthreads();
     float tout[K], aout[K];
     bool aact[K];
@@ -1201,7 +1208,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   // static + dynamic shared memory may exceed the 48 KB default
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
   int bps = 0;
-  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, iter_threads<R>(), zsmem));
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, persist_threads<R>(), zsmem));
   const uint32_t th = persistent_tile_height<R>(st.rows, st.cols, ctx->num_sms, bps);
   if (th == 0) return SRT3D_EAGAIN;
   const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
@@ -1221,8 +1228,8 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   uint32_t* flags = ctx->d_flags;
   void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &x0, &x1, &it, &tx, &thv, &flags};
   const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
-  SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles), dim3(iter_threads<R>()),
-                                                  args, zsmem, stream));
+  SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles),
+                                                  dim3(persist_threads<R>()), args, zsmem, stream));
   prof_end(ctx, KID_ITER_ALL, mk, stream);
   return SRT3D_OK;
   }
