@@ -168,7 +168,15 @@ srt3d_status srt3d_finalize(srt3d_ctx* ctx, const float* S, const uint32_t* n, u
  * (matched filter or given), then params->iters iterations of: sketched
  * gradient step on every point, APSS depth projection and intensity
  * smoothing / pruning over pixel-grid neighbourhoods (the RT3D iteration that
- * Sec. 3 adopts).
+ * Sec. 3 adopts). The matched-filter init takes k_max greedy passes: point k
+ * maximises s(t) = Re sum_l conj(hhat_l e^{i w_l t}) r_l over integer t, r the
+ * sketch minus the earlier points' fits, at least min_sep bins (circularly)
+ * from every earlier point; the argmax is exact over all T candidates. With
+ * regularize = 0 the iterations are the gradient step alone (pixelwise
+ * sketched estimate), optionally with W = Sigma_theta^-1 (params->weighting,
+ * Eq. 6). All iterations run in one cooperative launch when the frame's tiles
+ * fit on the device at once, else one launch per iteration; results are the
+ * same either way.
  *   z         device float [P][m][2], normalised sketches (srt3d_finalize)
  *   n         device uint32 [P] photon counts, P = rows * cols
  *   rows, cols  array size N_r x N_c, pixel p = r * cols + c
