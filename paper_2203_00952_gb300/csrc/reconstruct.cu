@@ -77,6 +77,7 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
                                           uint32_t entries, int two_level, float2* __restrict__ hh_out,
                                           float* __restrict__ misc, float2* s_tab) {
   __shared__ float s_h[kPrepChunk];
+  __shared__ float2 s_hh[32];
   load_table(s_tab, table, entries);
   const bool tl = two_level != 0;
   const float invT = 1.0f / float(T);
@@ -106,24 +107,33 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
       re += __shfl_xor_sync(0xffffffffu, re, off);
       im += __shfl_xor_sync(0xffffffffu, im, off);
     }
-    if (lane == 0) hh_out[l - 1] = make_float2(re / hs, im / hs);
+    if (lane == 0) {
+      hh_out[l - 1] = make_float2(re / hs, im / hs);
+      s_hh[warp] = make_float2(re / hs, im / hs);
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  // step-size sums over the harmonics, lane l - 1 of warp 0 taking harmonic l
+  if (warp == 0) {
     float sw = 0.f, sa = 0.f;
-    for (uint32_t l = 1; l <= m; ++l) {
-      const float2 v = hh_out[l - 1];
+    if (lane < m) {
+      const float2 v = s_hh[lane];
       const float a = sqrtf(v.x * v.x + v.y * v.y);
-      const float w = 6.283185307179586f * float(l) / float(T);
-      sw += w * w * a * (a + 2.f);
-      sa += a * a;
+      const float w = 6.283185307179586f * float(lane + 1u) / float(T);
+      sw = w * w * a * (a + 2.f);
+      sa = a * a;
     }
+    for (int off = 16; off; off >>= 1) {
+      sw += __shfl_xor_sync(0xffffffffu, sw, off);
+      sa += __shfl_xor_sync(0xffffffffu, sa, off);
+    }
+    if (lane != 0) return;
     misc[MISC_ETA_T] = 1.f / (2.f * sw);
     misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
     misc[MISC_E2] = sa;
     reinterpret_cast<unsigned*>(misc)[MISC_NMAX] = 0u;  // n_max: atomicMax by the init kernels
     reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
-    reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // grid barrier: generation
+    reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // (unused)
   }
 }
 
