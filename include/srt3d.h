@@ -285,6 +285,14 @@ srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t timeout_us, 
  * launch count. srt3d_profile_enable(ctx, 1) clears the totals and starts
  * recording, 0 stops. srt3d_profile_read() waits for the recorded events and
  * returns the totals of kernel `kernel` (an index < srt3d_kernel_count()). */
+/* Failure-detection self-test (the paper has no counterpart). Launches one
+ * CTA that runs the persistent iteration kernel's bounded grid-barrier wait on
+ * a barrier that nothing completes, with a limit of wait_cycles SM clock
+ * cycles (1..4e9): the wait gives up, latches the device timeout flag, and
+ * the next srt3d_sync returns SRT3D_ETIMEDOUT (clearing the flag). The
+ * context stays usable. */
+srt3d_status srt3d_selftest_wait_timeout(srt3d_ctx* ctx, uint64_t wait_cycles, void* stream);
+
 srt3d_status srt3d_profile_enable(srt3d_ctx* ctx, int enable);
 srt3d_status srt3d_profile_read(srt3d_ctx* ctx, uint32_t kernel, double* total_ms, uint64_t* launches);
 uint32_t srt3d_kernel_count(void);

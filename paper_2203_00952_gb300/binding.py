@@ -95,6 +95,7 @@ _SIGS = {
     "srt3d_status_string": (ctypes.c_char_p, [_i32]),
     "srt3d_last_error": (ctypes.c_char_p, [_vp]),
     "srt3d_sync": (_i32, [_vp, _vp]),
+    "srt3d_selftest_wait_timeout": (_i32, [_vp, ctypes.c_uint64, _vp]),
     "srt3d_hist_from_stream": (_i32, [_vp, _vp, _vp, _u64, _u32, _u32, _vp, _vp]),
     "srt3d_sketch_stream": (_i32, [_vp, _vp, _vp, _u64, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
     "srt3d_sketch_hist": (_i32, [_vp, _vp, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
@@ -283,6 +284,11 @@ def srt3d_kernel_count():
 
 def srt3d_kernel_name(kernel):
     return lib().srt3d_kernel_name(int(kernel)).decode()
+
+
+def srt3d_selftest_wait_timeout(ctx, wait_cycles, stream=None, check=True):
+    st = lib().srt3d_selftest_wait_timeout(ctx, int(wait_cycles), _stream(stream))
+    return _check(ctx, st, "srt3d_selftest_wait_timeout") if check else st
 
 
 def profile_totals(ctx):

@@ -1003,12 +1003,13 @@ __device__ __forceinline__ void grid_arrive(unsigned* bar) {
   }
 }
 
-__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32_t* flags, int* s_abort) {
+__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32_t* flags, int* s_abort,
+                                          long long limit = kGridWaitCycles) {
   if (threadIdx.x == 0) {
     volatile unsigned* cnt = bar;
     const long long t0 = clock64();
     while (*cnt < target) {
-      if (clock64() - t0 > kGridWaitCycles) {
+      if (clock64() - t0 > limit) {
         *s_abort = 1;
         atomicOr(flags, FLAG_DEVICE_TIMEOUT);
         break;
@@ -1019,6 +1020,17 @@ __device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32
   }
   __syncthreads();
   return *s_abort == 0;
+}
+
+// Diagnostic: the grid barrier's bounded wait on a counter that nothing
+// increments, with a short limit (see srt3d_selftest_wait_timeout).
+__device__ unsigned g_selftest_bar = 0u;
+
+__global__ void k_selftest_wait(uint32_t* flags, long long limit) {
+  __shared__ int s_abort;
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+  grid_wait(&g_selftest_bar, 1u, flags, &s_abort, limit);
 }
 
 // Post-gradient state of every point, exchanged between the CTAs of the
@@ -1556,4 +1568,13 @@ extern "C" srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z
     case 3: return run<3>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
     default: return run<4>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
   }
+}
+
+extern "C" srt3d_status srt3d_selftest_wait_timeout(srt3d_ctx* ctx, uint64_t wait_cycles, void* stream) {
+  if (!ctx) return SRT3D_EINVAL;
+  if (wait_cycles == 0 || wait_cycles > 4000000000ull)
+    return set_error(ctx, SRT3D_EINVAL, "wait_cycles must be in [1, 4e9]");
+  k_selftest_wait<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(ctx->d_flags, static_cast<long long>(wait_cycles));
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  return SRT3D_OK;
 }

@@ -218,3 +218,22 @@ def test_hist_sketch_fp32_of_stream_histogram_equals_stream_sketch(ctx):
     S_ref, n_ref = oracle.sketch_stream(fr.stamps, fr.offsets, spec.T, m)
     assert np.array_equal(counts(n), n_ref)
     assert sketch_err(S, n, S_ref, n_ref) <= TOL
+
+
+def test_bounded_device_wait_reports_timeout_and_context_stays_usable(ctx):
+    # a grid-barrier wait that can never complete gives up after ~1 ms of SM
+    # cycles, latches the device timeout flag and returns; the context keeps
+    # working afterwards
+    B.srt3d_selftest_wait_timeout(ctx, 2_000_000)
+    assert B.srt3d_sync(ctx, check=False) == B.SRT3D_ETIMEDOUT
+    assert B.srt3d_sync(ctx, check=False) == B.SRT3D_OK  # the flag was cleared
+    rng = np.random.default_rng(8)
+    per = [rng.integers(0, 1024, size=c) for c in (5, 300, 0, 17)]
+    stamps, offsets = csr(per)
+    S, n = gpu_sketch_stream(ctx, stamps, offsets, 1024, 6)
+    B.srt3d_sync(ctx)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, 1024, 6)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= TOL
+    with pytest.raises(B.SRT3DError):
+        B.srt3d_selftest_wait_timeout(ctx, 0)
