@@ -588,6 +588,35 @@ def mf_grid_spacing(T, m):
     return D
 
 
+# ----------------------------------------------------------------- multi-rank
+# Frames are independent, so N ranks are N replicas: each rank sketches and
+# reconstructs its own frame (seeded by its rank), the step time is the
+# maximum over ranks, and the value counts the photons of all ranks.
+
+def rank_frame(spec, rank):
+    """The frame of rank `rank` (independent seeded frames, no data exchange)."""
+    from paper_2203_00952_gb300 import synth
+
+    return synth.make_stream_frame(spec, synth.SEED_256x256, rank)
+
+
+def max_over_ranks(total_ms, world, device):
+    """Largest timed-region duration over the ranks (all ranks get it)."""
+    if world <= 1:
+        return float(total_ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, photons_per_frame, steps, total_ms):
+    """Whole-job photons per second: every rank processes one frame per step."""
+    return world * photons_per_frame * steps / (total_ms / 1e3)
+
+
 def kernel_work(name, N, P, m, T, K, iters):
     """Algorithmic work of one launch of kernel `name` (per
     photon / pixel / point figures). Returns (bound, amount, unit)."""
@@ -672,7 +701,7 @@ def gpu_arm(args):
         c = run_cpu_child(12.0)[0]
         cpu = {"value": c["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": c["sample"]}
 
-    fr = synth.make_stream_frame(spec, synth.SEED_256x256, rank)
+    fr = rank_frame(spec, rank)
     P, T = spec.num_pixels, spec.T
     N = int(fr.offsets[-1])
     stamps = torch.from_numpy(fr.stamps.view(np.int16)).to(dev)
@@ -730,11 +759,7 @@ def gpu_arm(args):
     prof = B.profile_totals(ctx)
     B.srt3d_profile_enable(ctx, False)
     clocks.stop()
-    total_ms = float(per_step.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(per_step.sum()), world, dev)
 
     # quality of the last step's result against the synthetic truth
     d = depth.cpu().numpy()
@@ -810,7 +835,7 @@ def gpu_arm(args):
         return
 
     ms_per_step = total_ms / args.steps
-    value = world * N * args.steps / (total_ms / 1e3)
+    value = job_value(world, N, args.steps, total_ms)
     hbm_peak, peak_kind = load_peaks()
     rooflines = {}
     for name, (ms, cnt) in prof.items():
