@@ -48,7 +48,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
-    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces", "pixelwise"],
+    ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces", "pixelwise",
+                                       "streamtc"],
                     default="all")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--batch-steps", type=int, default=5)
@@ -246,6 +247,51 @@ def hist_section(B, ctx, dev, steps, flush):
     out["peak_source"] = f"MEASURED_PEAKS.json ({peak_kind})"
     del hist, S, n
     torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------- stream via tensor cores
+def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
+    """Sketch of the 256x256 stamp stream two ways, at m = 10 and m = 32:
+    the CUDA-core stream kernel (srt3d_sketch_stream) and the composed
+    tensor-core route (device histogram, then the split-FP16 tcgen05 sketch;
+    srt3d_sketch_stream_tc). Device time per call (CUDA events, L2 evicted
+    between calls) and the error of the second against the first."""
+    import numpy as np
+    import torch
+
+    P, T = spec.num_pixels, spec.T
+    N = int(fr.offsets[-1])
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "stream_256x256_T4096", "photons": N}
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            fn()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        B.srt3d_sync(ctx, stream)
+        return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+    for m in (10, 32):
+        S1 = torch.empty(P, m, 2, device=dev)
+        S2 = torch.empty(P, m, 2, device=dev)
+        n1 = torch.empty(P, dtype=torch.int32, device=dev)
+        n2 = torch.empty(P, dtype=torch.int32, device=dev)
+        ms_cc = timed(lambda: B.srt3d_sketch_stream(ctx, stamps, offsets, T, m, 0, S1, n1, stream))
+        ms_tc = timed(lambda: B.srt3d_sketch_stream_tc(ctx, stamps, offsets, T, m, B.SRT3D_FP16_SPLIT, S2, n2,
+                                                       stream))
+        nn = torch.clamp(n1.to(torch.float32), min=1.0)[:, None]
+        err = float(((S2 - S1).norm(dim=-1) / nn).max().item())
+        out[f"m{m}"] = {"cuda_cores_ms": ms_cc, "tensor_cores_ms": ms_tc,
+                        "cuda_cores_photons_per_s": N / (ms_cc / 1e3), "tensor_cores_photons_per_s": N / (ms_tc / 1e3),
+                        "counts_equal": bool(torch.equal(n1, n2)), "max_diff_normalised": err}
+        del S1, S2, n1, n2
     return out
 
 
@@ -812,7 +858,9 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
     d2h = sum(o.nbytes for o in outs if o is not None)
 
-    hist = batch = surfaces = pixelwise = None
+    hist = batch = surfaces = pixelwise = stream_tc = None
+    if args.only in ("all", "streamtc") and rank == 0:
+        stream_tc = stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, args.hist_steps, flush)
     if args.only in ("all", "hist") and rank == 0:
         hist = hist_section(B, ctx, dev, args.hist_steps, flush)
     if args.only in ("all", "pixelwise") and rank == 0:
@@ -898,6 +946,7 @@ def gpu_arm(args):
         "batch": batch,
         "surfaces": surfaces,
         "pixelwise": pixelwise,
+        "stream_tc": stream_tc,
         "serving": serving,
     }
     print(json.dumps(out), flush=True)

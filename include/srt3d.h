@@ -158,6 +158,22 @@ srt3d_status srt3d_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const u
 srt3d_status srt3d_sketch_hist(srt3d_ctx* ctx, const uint16_t* hist, uint32_t num_pixels, uint32_t T,
                                uint32_t m, int precision, float* S, uint32_t* n, void* stream);
 
+/* The stream sketch of srt3d_sketch_stream (Sec. 2, Eq. 3) computed through
+ * the per-pixel histogram (Eq. 2, one bin per stamp value) and the tensor-core
+ * histogram sketch: its cost follows num_pixels x T and hardly m or the
+ * photons per pixel, so it is the faster route at large m or dense pixels.
+ *   stamps, offsets, num_stamps, num_pixels, S, n  as for srt3d_sketch_stream
+ *   (S and n are overwritten: no accumulate)
+ *   T          a multiple of 64 in [64, 65536]
+ *   m          1..32
+ *   precision  SRT3D_FP16_SPLIT or SRT3D_BF16 (as for srt3d_sketch_hist)
+ * The histogram (num_pixels x T uint16) lives in a context-owned device
+ * buffer: calls on one context must not overlap on different streams. A bin
+ * above 65535 counts saturates and is reported by srt3d_sync. */
+srt3d_status srt3d_sketch_stream_tc(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                    uint64_t num_stamps, uint32_t num_pixels, uint32_t T, uint32_t m,
+                                    int precision, float* S, uint32_t* n, void* stream);
+
 /* Normalise sketch states (Sec. 2, Eq. 3): z = S / n, and z = 0 where n = 0.
  *   S  device float [P][m][2];  n device uint32 [P];  z device float [P][m][2]
  *   (z may alias S). */

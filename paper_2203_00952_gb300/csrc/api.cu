@@ -158,6 +158,7 @@ void srt3d_destroy(srt3d_ctx* ctx) {
   for (auto& kv : ctx->tables) cudaFree(kv.second.dev);
   for (auto& kv : ctx->fourier) cudaFree(kv.second.ptr);
   if (ctx->rc_scratch.ptr) cudaFree(ctx->rc_scratch.ptr);
+  if (ctx->hist_scratch.ptr) cudaFree(ctx->hist_scratch.ptr);
   if (ctx->d_flags) cudaFree(ctx->d_flags);
   delete ctx;
 }

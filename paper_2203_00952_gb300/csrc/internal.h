@@ -115,6 +115,8 @@ struct srt3d_ctx {
   std::map<uint32_t, srt3d::PhaseTable> tables;
   // reconstruction scratch
   srt3d::DevBuf rc_scratch;
+  // device histogram of srt3d_sketch_stream_tc
+  srt3d::DevBuf hist_scratch;
   // histogram tensor-core operands keyed by (T, m, precision)
   std::map<std::tuple<uint32_t, uint32_t, int>, srt3d::DevBuf> fourier;
   std::mutex mu;  // guards tables/scratch growth for concurrent serving streams

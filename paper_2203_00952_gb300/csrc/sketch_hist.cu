@@ -149,3 +149,34 @@ extern "C" srt3d_status srt3d_sketch_hist(srt3d_ctx* ctx, const uint16_t* hist, 
   }
   return set_error(ctx, SRT3D_EINVAL, "unknown precision");
 }
+
+// Stream sketch through a device histogram and the tensor cores: the photons
+// of every pixel are binned (Sec. 2, Eq. 2, one bin per stamp value), and the
+// histogram sketch Y F (Eq. 3) is taken on the tensor cores. The cost depends
+// on P x T and hardly on m or on the photons per pixel, so it beats the
+// per-photon stream kernel at large m or dense pixels.
+extern "C" srt3d_status srt3d_sketch_stream_tc(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                               uint64_t num_stamps, uint32_t num_pixels, uint32_t T, uint32_t m,
+                                               int precision, float* S, uint32_t* n, void* stream) {
+  if (!ctx) return SRT3D_EINVAL;
+  if (!offsets || !S || !n || (num_stamps && !stamps)) return set_error(ctx, SRT3D_EINVAL, "NULL pointer");
+  if (T < 64 || T > 65536 || T % 64 != 0) return set_error(ctx, SRT3D_EINVAL, "T must be a multiple of 64 in [64, 65536]");
+  if (m < 1 || m > 32) return set_error(ctx, SRT3D_EINVAL, "m must be in [1, 32]");
+  if (precision != SRT3D_FP16_SPLIT && precision != SRT3D_BF16)
+    return set_error(ctx, SRT3D_EINVAL, "precision must be SRT3D_FP16_SPLIT or SRT3D_BF16");
+  if (num_stamps >= (1ull << 32)) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32");
+  if (reinterpret_cast<uintptr_t>(S) % 8) return set_error(ctx, SRT3D_EINVAL, "S must be 8-byte aligned");
+  if (num_pixels == 0) return SRT3D_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = size_t(num_pixels) * T * sizeof(uint16_t);
+  srt3d_status st;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    st = grow(ctx, &ctx->hist_scratch, bytes);
+  }
+  if (st != SRT3D_OK) return st;
+  uint16_t* hist = static_cast<uint16_t*>(ctx->hist_scratch.ptr);
+  st = launch_hist_from_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, hist, s);
+  if (st != SRT3D_OK) return st;
+  return launch_sketch_hist_tc(ctx, hist, num_pixels, T, m, precision, reinterpret_cast<float2*>(S), n, s);
+}

@@ -10,7 +10,7 @@ import oracle
 from paper_2203_00952_gb300 import binding as B
 from paper_2203_00952_gb300 import synth
 
-from gpu_util import counts, ctx, dev_hist, sketch_err, to_complex  # noqa: F401
+from gpu_util import counts, csr, ctx, dev_hist, dev_offsets, dev_stamps, sketch_err, to_complex  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -100,3 +100,26 @@ def test_full_size_512x512_histograms_sampled(ctx):
         del S, n
     del hist
     torch.cuda.empty_cache()
+
+
+
+@pytest.mark.parametrize("T,m,sizes", [(4096, 10, [1000, 0, 37, 5000, 3]), (1024, 32, [300, 301, 1, 0]),
+                                       (64, 3, [0, 12, 7])])
+def test_stream_sketch_through_tensor_cores(ctx, T, m, sizes):
+    # srt3d_sketch_stream_tc: device histogram of the stamp stream, then the
+    # tensor-core sketch; equals the oracle's stream sketch (FP16 split within
+    # 1e-5 normalised, counts exact)
+    rng = np.random.default_rng(T + m)
+    stamps, offsets = csr([rng.integers(0, T, size=c) for c in sizes])
+    P = len(sizes)
+    S = torch.zeros(P, m, 2, device="cuda")
+    n = torch.zeros(P, dtype=torch.int32, device="cuda")
+    sd = dev_stamps(stamps) if stamps.size else torch.zeros(8, dtype=torch.int16, device="cuda")[:0]
+    off = dev_offsets(offsets)
+    B.srt3d_sketch_stream_tc(ctx, sd, off, T, m, B.SRT3D_FP16_SPLIT, S, n)
+    B.srt3d_sync(ctx)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, T, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= 1e-5
+    with pytest.raises(B.SRT3DError):
+        B.srt3d_sketch_stream_tc(ctx, sd, off, 100, m, B.SRT3D_FP16_SPLIT, S, n)
