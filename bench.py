@@ -48,6 +48,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--hist-steps", type=int, default=10)
+    ap.add_argument("--hist-rows", type=int, default=512,
+                    help="side of the square histogram frame of the histogram section (512 = the workload)")
     ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces", "pixelwise",
                                        "streamtc"],
                     default="all")
@@ -199,18 +201,21 @@ class ClockSampler:
 HIST_M = 32
 
 
-def hist_section(B, ctx, dev, steps, flush):
+def hist_section(B, ctx, dev, steps, flush, rows=512):
     """Histogram sketch of the 512x512 x 4096-bin workload (10 000 counts/px,
     SBR 0.2, m = 32) in every precision: device time per launch (CUDA events,
     L2 evicted between launches), HBM roofline, tensor throughput, and the
-    error against the FP64 oracle on sampled pixels."""
+    error against the FP64 oracle on sampled pixels. `rows` < 512 runs the
+    same recipe on a rows x rows frame (a smaller case for profiling)."""
+    import dataclasses
+
     import numpy as np
     import torch
 
     import oracle
     from paper_2203_00952_gb300 import synth
 
-    spec = synth.frame_512x512_hist()
+    spec = dataclasses.replace(synth.frame_512x512_hist(), rows=rows, cols=rows)
     hist, _ = synth.make_hist_frame_torch(spec, synth.SEED_512x512, device=dev)
     P, T, m = spec.num_pixels, spec.T, HIST_M
     S = torch.empty(P, m, 2, device=dev)
@@ -221,7 +226,7 @@ def hist_section(B, ctx, dev, steps, flush):
     y_s = hist[torch.from_numpy(pix).to(dev)].cpu().numpy().view(np.uint16)
     S_ref, n_ref = oracle.sketch_hist(y_s, m)
     hbm_peak, peak_kind = load_peaks()
-    out = {"workload": "hist_512x512_T4096_m32", "photon_equivalents_per_frame": int(n_ref.mean() * P)}
+    out = {"workload": f"hist_{rows}x{rows}_T4096_m32", "photon_equivalents_per_frame": int(n_ref.mean() * P)}
     names = {B.SRT3D_FP32: "fp32", B.SRT3D_FP16_SPLIT: "fp16_split", B.SRT3D_BF16: "bf16"}
     for prec in (B.SRT3D_FP16_SPLIT, B.SRT3D_BF16, B.SRT3D_FP32):
         for _ in range(2):
@@ -733,7 +738,7 @@ def gpu_arm(args):
         # histogram path alone (for profiling): no step timing, no baseline
         ctx = B.srt3d_create(local)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-        res = hist_section(B, ctx, dev, args.hist_steps, flush)
+        res = hist_section(B, ctx, dev, args.hist_steps, flush, args.hist_rows)
         B.srt3d_destroy(ctx)
         if rank == 0:
             print(json.dumps({"hist_sketch": res}), flush=True)

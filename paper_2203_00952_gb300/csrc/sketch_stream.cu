@@ -358,50 +358,126 @@ __global__ void k_finalize_batch(const BatchFrame* __restrict__ frames) {
   f.S[i] = cnt ? make_float2(s.x / nf, s.y / nf) : make_float2(0.f, 0.f);
 }
 
-// One CTA per pixel at a time; u32 counters in shared memory over a window of
-// at most kHistWindow bins (the pixel's stamps are re-scanned per window).
-constexpr uint32_t kHistWindow = 16384;
+// One warp per pixel at a time, with 8 KB of shared-memory counters per warp
+// and no block-wide barrier. A pixel with at most 65535 photons (no bin can
+// exceed a u16) counts into packed u16 pairs (bin b in half b & 1 of word
+// b / 2), 4096 bins per window: the counter words are then the output row
+// itself. A pixel with more photons counts into u32 counters, 2048 bins per
+// window, saturated to 65535 (flagged) on output. Each window re-scans the
+// pixel's stamps (T <= 4096 is one window). Stamps are read 8 per lane in
+// flight. Rows are written 16 bytes per store when T is a multiple of 8 and
+// the output is 16-byte aligned.
+constexpr uint32_t kHistWarps = 4;            // warps per CTA
+constexpr uint32_t kHistWords = 2048;         // u32 counter words per warp (8 KB)
+constexpr uint32_t kHistBins16 = 2 * kHistWords;
+constexpr uint32_t kHistBins32 = kHistWords;
+constexpr int kHistUnroll = 8;
 
-__global__ void __launch_bounds__(kBlock) k_hist_from_stream(const uint16_t* __restrict__ stamps,
-                                                             const uint32_t* __restrict__ offsets,
-                                                             uint32_t num_stamps, uint32_t P, uint32_t T,
-                                                             uint16_t* __restrict__ hist,
-                                                             uint32_t* __restrict__ flags) {
-  extern __shared__ uint32_t s_cnt[];
-  for (uint32_t p = blockIdx.x; p < P; p += gridDim.x) {
-    uint32_t s = __ldg(offsets + p), e = __ldg(offsets + p + 1);
-    if (e < s || e > num_stamps) {
-      if (threadIdx.x == 0) atomicOr(flags, FLAG_OFFSETS);
-      s = e = 0;
+__device__ __forceinline__ uint32_t sat16(uint32_t c, bool& over) {
+  over |= c > 65535u;
+  return min(c, 65535u);
+}
+
+// Count the stamps [s, e) that fall in [b0, b0 + nb) into cnt (packed u16
+// pairs when PACKED, else u32).
+template <bool PACKED>
+__device__ __forceinline__ void hist_count(const uint16_t* __restrict__ stamps, uint64_t s, uint64_t e, uint32_t T,
+                                           uint32_t b0, uint32_t nb, uint32_t* cnt, uint32_t lane, bool& bad) {
+  for (uint64_t i0 = s; i0 < e; i0 += 32u * kHistUnroll) {
+    uint32_t x[kHistUnroll];
+#pragma unroll
+    for (int k = 0; k < kHistUnroll; ++k) {
+      const uint64_t i = i0 + lane + 32u * k;
+      x[k] = i < e ? uint32_t(__ldg(stamps + i)) : 0xffffffffu;
     }
-    for (uint32_t b0 = 0; b0 < T; b0 += kHistWindow) {
-      const uint32_t nb = min(kHistWindow, T - b0);
-      for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) s_cnt[i] = 0u;
-      __syncthreads();
-      bool bad = false;
-      for (uint32_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const uint32_t x = __ldg(stamps + i);
-        if (x >= T)
-          bad = true;
-        else if (x - b0 < nb)
-          atomicAdd(&s_cnt[x - b0], 1u);
+#pragma unroll
+    for (int k = 0; k < kHistUnroll; ++k) {
+      if (x[k] == 0xffffffffu) continue;
+      if (x[k] >= T) {
+        bad = true;
+        continue;
       }
-      if (bad && b0 == 0) atomicOr(flags, FLAG_STAMP_RANGE);
-      __syncthreads();
-      uint16_t* row = hist + size_t(p) * T + b0;
-      bool over = false;
-      for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) {
-        uint32_t c = s_cnt[i];
-        if (c > 65535u) {
-          over = true;
-          c = 65535u;
-        }
-        row[i] = uint16_t(c);
+      const uint32_t b = x[k] - b0;
+      if (b < nb) {
+        if (PACKED)
+          atomicAdd(&cnt[b >> 1], 1u << ((b & 1u) << 4));
+        else
+          atomicAdd(&cnt[b], 1u);
       }
-      if (over) atomicOr(flags, FLAG_COUNT_RANGE);
-      __syncthreads();
     }
   }
+}
+
+__global__ void __launch_bounds__(kHistWarps * 32) k_hist_from_stream(const uint16_t* __restrict__ stamps,
+                                                                      const uint32_t* __restrict__ offsets,
+                                                                      uint32_t num_stamps, uint32_t P, uint32_t T,
+                                                                      uint16_t* __restrict__ hist,
+                                                                      uint32_t* __restrict__ flags) {
+  extern __shared__ __align__(16) uint32_t s_hist[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint32_t* cnt = s_hist + warp * kHistWords;
+  uint4* cnt4 = reinterpret_cast<uint4*>(cnt);
+  for (uint32_t j = lane; j < kHistWords / 4u; j += 32u) cnt4[j] = make_uint4(0u, 0u, 0u, 0u);
+  __syncwarp();
+  const bool vec = (T % 8u) == 0u && (reinterpret_cast<uintptr_t>(hist) % 16u) == 0u;
+  bool bad = false, over = false, bad_off = false;
+  const uint64_t W = uint64_t(gridDim.x) * kHistWarps;
+  for (uint64_t p = uint64_t(blockIdx.x) * kHistWarps + warp; p < P; p += W) {
+    uint32_t s = __ldg(offsets + p), e = __ldg(offsets + p + 1);
+    if (e < s || e > num_stamps) {
+      bad_off = true;
+      s = e = 0u;
+    }
+    uint16_t* row = hist + size_t(p) * T;
+    if (e - s <= 65535u) {
+      for (uint32_t b0 = 0; b0 < T; b0 += kHistBins16) {
+        const uint32_t nb = min(kHistBins16, T - b0);
+        hist_count<true>(stamps, s, e, T, b0, nb, cnt, lane, bad);
+        __syncwarp();
+        if (vec) {
+          uint4* r4 = reinterpret_cast<uint4*>(row + b0);
+          for (uint32_t j = lane; j < nb / 8u; j += 32u) {
+            r4[j] = cnt4[j];
+            cnt4[j] = make_uint4(0u, 0u, 0u, 0u);
+          }
+        } else {
+          for (uint32_t j = lane; j < nb; j += 32u) row[b0 + j] = uint16_t(cnt[j >> 1] >> ((j & 1u) << 4));
+          __syncwarp();
+          for (uint32_t j = lane; j < (nb + 1u) / 2u; j += 32u) cnt[j] = 0u;
+        }
+        __syncwarp();
+      }
+    } else {
+      for (uint32_t b0 = 0; b0 < T; b0 += kHistBins32) {
+        const uint32_t nb = min(kHistBins32, T - b0);
+        hist_count<false>(stamps, s, e, T, b0, nb, cnt, lane, bad);
+        __syncwarp();
+        if (vec) {
+          uint4* r4 = reinterpret_cast<uint4*>(row + b0);
+          for (uint32_t j = lane; j < nb / 8u; j += 32u) {
+            const uint4 a = cnt4[2 * j], b = cnt4[2 * j + 1];
+            cnt4[2 * j] = make_uint4(0u, 0u, 0u, 0u);
+            cnt4[2 * j + 1] = make_uint4(0u, 0u, 0u, 0u);
+            uint4 o;
+            o.x = sat16(a.x, over) | (sat16(a.y, over) << 16);
+            o.y = sat16(a.z, over) | (sat16(a.w, over) << 16);
+            o.z = sat16(b.x, over) | (sat16(b.y, over) << 16);
+            o.w = sat16(b.z, over) | (sat16(b.w, over) << 16);
+            r4[j] = o;
+          }
+        } else {
+          for (uint32_t j = lane; j < nb; j += 32u) {
+            row[b0 + j] = uint16_t(sat16(cnt[j], over));
+            cnt[j] = 0u;
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (bad_off) atomicOr(flags, FLAG_OFFSETS);
+  if (bad) atomicOr(flags, FLAG_STAMP_RANGE);
+  if (over) atomicOr(flags, FLAG_COUNT_RANGE);
 }
 
 }  // namespace
@@ -495,16 +571,18 @@ srt3d_status launch_finalize_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, u
 srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                      uint64_t num_stamps, uint32_t P, uint32_t T, uint16_t* hist,
                                      cudaStream_t stream) {
-  const size_t smem = size_t(std::min(T, kHistWindow)) * sizeof(uint32_t);
+  constexpr uint32_t threads = kHistWarps * 32;
+  const size_t smem = size_t(kHistWarps) * kHistWords * sizeof(uint32_t);
   int bps = 0;
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hist_from_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(kHistWindow * sizeof(uint32_t))));
-  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hist_from_stream, kBlock, smem));
+                                           int(smem)));
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_hist_from_stream, threads, smem));
   if (bps < 1) bps = 1;
-  const uint32_t grid = uint32_t(std::min<uint64_t>(P, uint64_t(ctx->num_sms) * bps));
+  const uint64_t want = (uint64_t(P) + kHistWarps - 1) / kHistWarps;
+  const uint32_t grid = uint32_t(std::min<uint64_t>(want, uint64_t(ctx->num_sms) * bps));
   const ProfMark mk = prof_begin(ctx, KID_HIST_FROM_STREAM, stream);
-  k_hist_from_stream<<<grid, kBlock, smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, hist,
-                                                     ctx->d_flags);
+  k_hist_from_stream<<<grid, threads, smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, hist,
+                                                      ctx->d_flags);
   prof_end(ctx, KID_HIST_FROM_STREAM, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;

@@ -145,7 +145,8 @@ def test_invalid_arguments_rejected_synchronously(ctx):
 
 
 @pytest.mark.parametrize("T,sizes", [(1024, [0, 1, 100, 3000]), (4613, [5, 0, 2000]), (65536, [1000, 3, 0]),
-                                     (16385, [300, 300])])
+                                     (16385, [300, 300]), (5000, [70000, 100]), (4096, [70000, 0, 5]),
+                                     (8, [65535, 65536, 1])])
 def test_hist_from_stream_bit_exact(ctx, T, sizes):
     rng = np.random.default_rng(T)
     per = [rng.integers(0, T, size=c) for c in sizes]
@@ -156,6 +157,19 @@ def test_hist_from_stream_bit_exact(ctx, T, sizes):
     B.srt3d_sync(ctx)
     ref = oracle.hist_from_stream(stamps, offsets, T)
     assert np.array_equal(hist.cpu().numpy().view(np.uint16), ref)
+
+
+def test_hist_from_stream_unaligned_output_bit_exact(ctx):
+    # an output row start that is only 2-byte aligned takes the scalar stores
+    T = 1024
+    rng = np.random.default_rng(11)
+    stamps, offsets = csr([rng.integers(0, T, size=c) for c in (500, 0, 77)])
+    buf = torch.zeros(3 * T + 1, dtype=torch.int16, device="cuda")
+    B.srt3d_hist_from_stream(ctx, dev_stamps(stamps), dev_offsets(offsets), T, buf[1:])
+    B.srt3d_sync(ctx)
+    assert int(buf[0].item()) == 0
+    assert np.array_equal(buf[1:].cpu().numpy().view(np.uint16).reshape(3, T),
+                          oracle.hist_from_stream(stamps, offsets, T))
 
 
 def test_hist_from_stream_32x32_frame_bit_exact(ctx):
