@@ -3,16 +3,20 @@
 //   F^T[2(l-1)+1][b] = sin(...), N = 2m rounded up to 16 (x2 for the split).
 //
 // Persistent, warp-specialised CTA (512 threads, one per SM), M = 128 pixels
-// per tile, K = 64 bins per pipeline stage:
+// per tile, K = 64 bins per pipeline stage, as many stages (up to 8) as fit in
+// shared memory next to one shared A2 slot:
 //   warp 0      TMA producer: Y tile [128 x 64] u16 and F^T tile [N x 64],
 //               both 128-byte swizzled (the canonical K-major operand layout)
 //   warps 4-11  converters: two threads per pixel row convert the stage in
 //               place to FP16 (exact for counts <= 2048; larger counts are
-//               split exactly into (y & ~31) in A and (y & 31) in a second
-//               operand A2) or to BF16; they also count the row's photons (n)
-//               in integers
+//               split exactly into (y & ~31) in A and (y & 31) in the A2
+//               slot, shared by all stages) or to BF16; they also count the
+//               row's photons (n) in integers
 //   warp 1      MMA issuer: tcgen05.mma.kind::f16 into a double-buffered FP32
 //               accumulator in TMEM; A2 only for stages that hold a count > 2048
+//               (a converter writes the A2 slot only after the MMAs of the
+//               previous stage have completed, so big counts serialise the
+//               pipeline while they last and cost nothing otherwise)
 //   warps 12-15 epilogue: tcgen05.ld of the accumulator, hi + lo, store S
 // SRT3D_FP16_SPLIT uses F = F_hi + F_lo (both FP16, stacked along N, one MMA
 // computes both products); SRT3D_BF16 uses a single BF16 F and BF16 counts.
@@ -152,10 +156,11 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N, uint32
   return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
 }
 
+constexpr int kMaxStages = 8;
+
 template <int PREC>
 struct TcCfg {
   static constexpr bool kSplit = (PREC == SRT3D_FP16_SPLIT);
-  static constexpr int kStages = kSplit ? 4 : 6;
 };
 
 // ------------------------------------------------------------------ the kernel
@@ -163,39 +168,38 @@ struct TcCfg {
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_hist_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapF,
-                     uint32_t P, uint32_t T, uint32_t m, uint32_t N2, uint32_t ncols_alloc,
+                     uint32_t P, uint32_t T, uint32_t m, uint32_t N2, uint32_t ncols_alloc, uint32_t ST,
                      float2* __restrict__ S, uint32_t* __restrict__ n, uint32_t* __restrict__ gflags) {
   using Cfg = TcCfg<PREC>;
-  constexpr int ST = Cfg::kStages;
   constexpr bool kSplit = Cfg::kSplit;
   const uint32_t N = kSplit ? 2u * N2 : N2;  // MMA N (rows of F^T per stage)
   const uint32_t b_bytes = N * 128u;
-  const uint32_t stage_bytes = kABytes * (kSplit ? 2u : 1u) + b_bytes;
+  const uint32_t stage_bytes = kABytes + b_bytes;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + ST * stage_bytes);
-  // barrier slots: full[ST], conv[ST], empty[ST], tfull[2], tempty[2], drain
+  uint8_t* a2_slot = base + ST * stage_bytes;  // FP16 split only
+  uint64_t* bars = reinterpret_cast<uint64_t*>(a2_slot + (kSplit ? kABytes : 0u));
+  // barrier slots: full[8], conv[8], empty[8], tfull[2], tempty[2], drain
   uint64_t* full = bars;
-  uint64_t* conv = bars + ST;
-  uint64_t* empty = bars + 2 * ST;
-  uint64_t* tfull = bars + 3 * ST;
+  uint64_t* conv = bars + kMaxStages;
+  uint64_t* empty = bars + 2 * kMaxStages;
+  uint64_t* tfull = bars + 3 * kMaxStages;
   uint64_t* tempty = tfull + 2;
   uint64_t* drain = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-  uint32_t* split_gen = tmem_slot + 1;  // [ST]
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(split_gen + ST);
+  uint32_t* split_gen = tmem_slot + 1;  // [8]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(split_gen + kMaxStages);
 
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t ntiles = (P + kTileM - 1) / kTileM;
   const uint32_t KT = T / kTileK;
 
   auto sA = [&](uint32_t s) { return base + s * stage_bytes; };
-  auto sA2 = [&](uint32_t s) { return base + s * stage_bytes + kABytes; };
-  auto sB = [&](uint32_t s) { return base + s * stage_bytes + kABytes * (kSplit ? 2u : 1u); };
+  auto sB = [&](uint32_t s) { return base + s * stage_bytes + kABytes; };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < ST; ++s) {
+    for (uint32_t s = 0; s < ST; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&conv[s]), 256);
       mbar_init(smem_u32(&empty[s]), 1);
@@ -223,18 +227,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
     if (lane == 0) {
-      uint32_t it = 0;
+      uint32_t it = 0, s = 0, ph = 0;
       for (uint32_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
-          const uint32_t s = it % ST, ph = (it / ST) & 1u;
           if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, gflags)) break;
           mbar_arrive_expect_tx(smem_u32(&full[s]), kABytes + b_bytes);
           tma_load_2d(smem_u32(sA(s)), &mapY, smem_u32(&full[s]), int(kt * kTileK), int(tile * kTileM));
           tma_load_2d(smem_u32(sB(s)), &mapF, smem_u32(&full[s]), int(kt * kTileK), 0);
+          if (++s == ST) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
       }
       // no copy may be in flight when the CTA leaves: wait for the last stages issued
-      const uint32_t first = it > uint32_t(ST) ? it - ST : 0u;
+      const uint32_t first = it > ST ? it - ST : 0u;
       for (uint32_t j = first; j < it; ++j) {
         const uint32_t s = j % ST, ph = (j / ST) & 1u;
         const long long t0 = clock64();
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       const uint32_t idesc = make_idesc(kTileM, N, PREC == SRT3D_BF16 ? 1u : 0u);
       const uint32_t acc_cols = ncols_alloc / 2;
-      uint32_t it = 0, lt = 0;
+      uint32_t it = 0, lt = 0, s = 0, ph = 0;
       bool ok = true;
       for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
         const uint32_t acc = lt & 1u, aph = (lt >> 1) & 1u;
@@ -255,12 +262,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + acc * acc_cols;
         for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
-          const uint32_t s = it % ST, ph = (it / ST) & 1u;
           if (!(ok = mbar_wait(smem_u32(&conv[s]), ph, abort_flag, gflags))) break;
           tc_fence_after();
           const bool split = kSplit && split_gen[s] == it;
           const uint64_t da = sw128_desc(smem_u32(sA(s)));
-          const uint64_t da2 = sw128_desc(smem_u32(sA2(s)));
+          const uint64_t da2 = sw128_desc(smem_u32(a2_slot));
           const uint64_t db = sw128_desc(smem_u32(sB(s)));
 #pragma unroll
           for (uint32_t k = 0; k < kTileK / 16; ++k) {
@@ -269,6 +275,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (split) umma_f16(d_tmem, da2 + 2 * k, db + 2 * k, idesc, 1u);
           }
           umma_commit(smem_u32(&empty[s]));
+          if (++s == ST) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
         if (!ok) break;
         umma_commit(smem_u32(&tfull[acc]));
@@ -287,31 +297,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     // is elementwise, so the order does not matter. Small counts take an exact
     // bit-pattern path (FP16: (0x6400 | y) - 1024 for y < 1024; BF16:
     // (0x4300 | y) - 128 for y < 128); others take the rounding conversion.
-    // A2 (FP16 split) starts zeroed and a thread rewrites its A2 chunks only
-    // while they hold, or last held, a count above 2048.
+    // The A2 slot (FP16 split) starts zeroed; a thread rewrites its A2 chunks
+    // only while they hold, or last held, a count above 2048, and only after
+    // the previous stage's MMAs, the last that may have read the slot, have
+    // completed (the empty barrier of that stage's slot).
     const uint32_t ct = threadIdx.x - 128u;
     const uint32_t row = ct & 127u, c0 = (ct >> 7) * 4u;
     const uint32_t sw = row & 7u;
-    uint32_t dirty = 0u;  // bit s: this thread's A2 chunks of stage slot s are nonzero
+    bool dirty = false;  // this thread's A2 chunks are nonzero
     if (kSplit) {
-      for (int s2 = 0; s2 < ST; ++s2) {
-        uint8_t* ra2 = sA2(s2) + row * 128u;
+      uint8_t* ra2 = a2_slot + row * 128u;
 #pragma unroll
-        for (uint32_t c = 0; c < 4; ++c)
-          *reinterpret_cast<uint4*>(ra2 + (((c0 + c) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
-      }
+      for (uint32_t c = 0; c < 4; ++c)
+        *reinterpret_cast<uint4*>(ra2 + (((c0 + c) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
       fence_proxy_async_smem();
     }
-    constexpr uint32_t kMagicLimit = kSplit ? 0x03FF03FFu : 0x007F007Fu;
-    uint32_t it = 0;
+    // a halfword exceeds the bit-pattern limit (1023 FP16, 127 BF16) iff one
+    // of its bits above the limit is set: test the OR of the stage's words
+    constexpr uint32_t kOverMask = kSplit ? 0xFC00FC00u : 0xFF80FF80u;
+    uint32_t it = 0, s = 0, ph = 0;
+    uint32_t ps = 0, pph = 0;  // slot and phase parity of stage it - 1
     bool ok = true;
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       uint32_t cnt = 0;
       for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
-        const uint32_t s = it % ST, ph = (it / ST) & 1u;
         if (!(ok = mbar_wait(smem_u32(&full[s]), ph, abort_flag, gflags))) break;
         uint8_t* ra = sA(s) + row * 128u;
-        uint8_t* ra2 = sA2(s) + row * 128u;
+        uint8_t* ra2 = a2_slot + row * 128u;
         uint32_t w[16];
 #pragma unroll
         for (uint32_t c = 0; c < 4; ++c) {
@@ -321,12 +333,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           w[4 * c + 2] = v.z;
           w[4 * c + 3] = v.w;
         }
-        uint32_t over = 0u, big = 0u;
+        uint32_t any = 0u, big = 0u;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           cnt = __dp2a_lo(w[q], 0x00000101u, cnt);  // + low half + high half
-          over |= __vcmpgtu2(w[q], kMagicLimit);
-          if (kSplit) big |= __vcmpgtu2(w[q], 0x08000800u);
+          any |= w[q];
+        }
+        const uint32_t over = any & kOverMask;
+        if (kSplit && over != 0u) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) big |= __vcmpgtu2(w[q], 0x08000800u);
         }
         uint32_t hi[16], lo[16];
         if (over == 0u) {
@@ -373,7 +389,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         const bool large = kSplit && big != 0u;
-        const bool rewrite_a2 = kSplit && (large || ((dirty >> s) & 1u));
+        const bool rewrite_a2 = kSplit && (large || dirty);
+        // Stage it - 1's MMAs complete phase pph of empty[ps]. That barrier is
+        // at most one phase behind it: this thread converted stage it - 1,
+        // whose data the producer loaded only after the previous phase
+        // completed. So the parity wait cannot alias an older phase.
+        if (rewrite_a2 && it > 0u && !(ok = mbar_wait(smem_u32(&empty[ps]), pph, abort_flag, gflags))) break;
 #pragma unroll
         for (uint32_t c = 0; c < 4; ++c) {
           const uint32_t off = ((c0 + c) ^ sw) << 4;
@@ -382,11 +403,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4*>(ra2 + off) = make_uint4(lo[4 * c], lo[4 * c + 1], lo[4 * c + 2], lo[4 * c + 3]);
         }
         if (kSplit) {
-          dirty = large ? (dirty | (1u << s)) : (dirty & ~(1u << s));
+          dirty = large;
           if (large) split_gen[s] = it;
         }
         fence_proxy_async_smem();
         mbar_arrive(smem_u32(&conv[s]));
+        ps = s;
+        pph = ph;
+        if (++s == ST) {
+          s = 0;
+          ph ^= 1u;
+        }
       }
       if (!ok) break;
       const uint32_t p = tile * kTileM + row;
@@ -526,16 +553,21 @@ srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_
   CUtensorMap mapY, mapF;
   if (!encode_map(&mapY, hist, P, T, kTileM) || !encode_map(&mapF, F, N, T, N))
     return set_error(ctx, SRT3D_ECUDA, "cuTensorMapEncodeTiled failed");
-  const size_t stage_bytes = size_t(kABytes) * (Cfg::kSplit ? 2 : 1) + size_t(N) * 128;
-  const size_t smem = 1024 + Cfg::kStages * stage_bytes + 256;
-  if (smem > ctx->smem_optin) return set_error(ctx, SRT3D_EINVAL, "tensor-core tile does not fit shared memory");
+  // stages: as many as fit (at most kMaxStages) beside the A2 slot, the
+  // 1024-byte alignment pad and the barrier block
+  const size_t stage_bytes = size_t(kABytes) + size_t(N) * 128;
+  const size_t fixed = 1024 + (Cfg::kSplit ? size_t(kABytes) : 0) + 512;
+  const size_t fit = ctx->smem_optin > fixed ? (ctx->smem_optin - fixed) / stage_bytes : 0;
+  const uint32_t ST = uint32_t(std::min<size_t>(kMaxStages, fit));
+  if (ST < 2) return set_error(ctx, SRT3D_EINVAL, "tensor-core tile does not fit shared memory");
+  const size_t smem = fixed + ST * stage_bytes;
   auto kfn = k_sketch_hist_tc<PREC>;
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const uint32_t ntiles = (P + kTileM - 1) / kTileM;
   const uint32_t grid = std::min<uint32_t>(ntiles, uint32_t(ctx->num_sms));
   SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(n, 0, size_t(P) * sizeof(uint32_t), stream));
   const ProfMark mk = prof_begin(ctx, KID_SKETCH_HIST_TC, stream);
-  kfn<<<grid, kThreads, smem, stream>>>(mapY, mapF, P, T, m, N2, ncols_alloc, S, n, ctx->d_flags);
+  kfn<<<grid, kThreads, smem, stream>>>(mapY, mapF, P, T, m, N2, ncols_alloc, ST, S, n, ctx->d_flags);
   prof_end(ctx, KID_SKETCH_HIST_TC, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;

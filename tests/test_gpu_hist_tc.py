@@ -54,6 +54,21 @@ def test_fp16_split_exact_for_counts_above_2048(ctx):
     assert sketch_err(S, n, S_ref, n_ref) <= SPLIT_TOL
 
 
+@pytest.mark.parametrize("P,T,m,frac", [(1000, 4096, 32, 0.01), (300, 1024, 10, 1.0), (700, 2048, 3, 0.2)])
+def test_fp16_split_counts_above_2048_in_many_stages(ctx, P, T, m, frac):
+    # big counts scattered over many tiles and pipeline stages (every stage
+    # when frac = 1): the A2 slot shared by the stages must carry exactly the
+    # low parts of its own stage
+    rng = np.random.default_rng(int(frac * 100) + T)
+    y = rng.poisson(3.0, size=(P, T)).astype(np.uint16)
+    big = rng.random((P, T)) < frac
+    y[big] = rng.integers(2049, 65536, size=int(big.sum())).astype(np.uint16)
+    S, n = run(ctx, y, m, B.SRT3D_FP16_SPLIT)
+    S_ref, n_ref = oracle.sketch_hist(y, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= SPLIT_TOL
+
+
 @pytest.mark.parametrize("P,T,m", [(1, 64, 1), (130, 1024, 10), (300, 4096, 32)])
 def test_bf16_reported_error(ctx, P, T, m):
     rng = np.random.default_rng(P * 3 + m)
