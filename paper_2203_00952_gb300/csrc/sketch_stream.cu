@@ -94,14 +94,40 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   return v;
 }
 
+// The 8 stamps of one 16-byte word.
+template <int M, bool TL>
+__device__ __forceinline__ void word_photons(pf2 (&acc)[M], const uint4 v, const float2* s_tab, uint32_t T,
+                                             float invT, bool& bad) {
+  const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
+                         v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
+  uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
+  if (mx < T) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (x[i] < T)
+        add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+      else
+        bad = true;
+    }
+  }
+}
+
 // All photons of one pixel for lane gl of its group: the loose stamps one
-// per lane, then whole words. Returns whether a stamp was >= T.
+// per lane, then whole words. The lane's first word is requested before the
+// loose stamps are processed and each next word before the current one, so
+// one load is always in flight. Returns whether a stamp was >= T.
 template <int M, bool TL>
 __device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const uint4* __restrict__ words,
                                               const uint16_t* __restrict__ half, uint32_t a, uint32_t b,
                                               uint32_t nh, uint32_t nl, uint32_t ts, uint32_t wa, uint32_t wb,
                                               uint32_t T, float invT, uint32_t G, uint32_t gl, const float2* s_tab) {
   bool bad = false;
+  uint32_t w = wa + gl;
+  uint4 v = make_uint4(0u, 0u, 0u, 0u);
+  if (w < wb) v = ld_stream(words + w);
   for (uint32_t i = gl; i < nl; i += G) {
     const uint32_t x = __ldg(half + (i < nh ? a + i : ts + (i - nh)));
     if (x < T)
@@ -109,23 +135,13 @@ __device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const uint4* __rest
     else
       bad = true;
   }
-  for (uint32_t w = wa + gl; w < wb; w += G) {
-    const uint4 v = ld_stream(words + w);
-    const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
-                           v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
-    uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
-    if (mx < T) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) add_photon<M, TL>(acc, x[i], s_tab, T, invT);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        if (x[i] < T)
-          add_photon<M, TL>(acc, x[i], s_tab, T, invT);
-        else
-          bad = true;
-      }
-    }
+  while (w < wb) {
+    const uint32_t wn = w + G;
+    uint4 vn = make_uint4(0u, 0u, 0u, 0u);
+    if (wn < wb) vn = ld_stream(words + wn);
+    word_photons<M, TL>(acc, v, s_tab, T, invT, bad);
+    v = vn;
+    w = wn;
   }
   return bad;
 }
@@ -200,14 +216,13 @@ __device__ __forceinline__ void store_sums(const pf2 (&acc)[M], uint32_t gl, uns
 // One pixel of the stream, processed by a group of G lanes: coalesced 16-byte
 // words from the aligned base, per-lane partial sums, xor-shuffle reduction,
 // store (or accumulate) of S[p][0..m) and n[p].
+// (s, e) = offsets[p], offsets[p + 1], already loaded by the caller.
 template <int M>
-__device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, uint32_t shift,
-                                             const uint32_t* __restrict__ offsets, uint32_t num_stamps, uint32_t p,
-                                             uint32_t T, float invT, uint32_t m, uint32_t G, uint32_t gl,
-                                             unsigned gmask, int accumulate, const float2* s_tab, bool tl,
-                                             float2* __restrict__ S, uint32_t* __restrict__ n,
-                                             uint32_t* __restrict__ flags) {
-  uint32_t s = __ldg(offsets + p), e = __ldg(offsets + p + 1);
+__device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, uint32_t shift, uint32_t s,
+                                             uint32_t e, uint32_t num_stamps, uint32_t p, uint32_t T, float invT,
+                                             uint32_t m, uint32_t G, uint32_t gl, unsigned gmask, int accumulate,
+                                             const float2* s_tab, bool tl, float2* __restrict__ S,
+                                             uint32_t* __restrict__ n, uint32_t* __restrict__ flags) {
   if (e < s || e > num_stamps) {
     if (gl == 0) atomicOr(flags, FLAG_OFFSETS);
     s = e = 0;
@@ -236,7 +251,7 @@ __device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, ui
 }
 
 template <int M>
-__global__ void __launch_bounds__(kBlock, M <= 10 ? 5 : (M <= 16 ? 3 : 2)) k_sketch_stream(
+__global__ void __launch_bounds__(kBlock, M <= 10 ? 4 : (M <= 16 ? 3 : 2)) k_sketch_stream(
     const uint16_t* __restrict__ stamps, const uint32_t* __restrict__ offsets, uint32_t num_stamps,
     uint32_t P, uint32_t T, uint32_t m, int glog2, int accumulate, const float2* __restrict__ table,
     uint32_t tab_entries, int two_level, float2* __restrict__ S, uint32_t* __restrict__ n,
@@ -255,9 +270,21 @@ __global__ void __launch_bounds__(kBlock, M <= 10 ? 5 : (M <= 16 ? 3 : 2)) k_ske
   const uintptr_t addr = reinterpret_cast<uintptr_t>(stamps);
   const uint4* words = reinterpret_cast<const uint4*>(addr & ~uintptr_t(15));
   const uint32_t shift = uint32_t(addr & 15u) >> 1;
-  for (uint32_t p = gid; p < P; p += ngroups)
-    sketch_pixel<M>(words, shift, offsets, num_stamps, p, T, invT, m, G, gl, gmask, accumulate, s_tab, tl, S, n,
+  // the next pixel's offsets are requested before the current pixel runs
+  uint32_t sn = 0, en = 0;
+  if (gid < P) {
+    sn = __ldg(offsets + gid);
+    en = __ldg(offsets + gid + 1);
+  }
+  for (uint32_t p = gid; p < P; p += ngroups) {
+    const uint32_t s = sn, e = en;
+    if (uint64_t(p) + ngroups < P) {
+      sn = __ldg(offsets + p + ngroups);
+      en = __ldg(offsets + p + ngroups + 1);
+    }
+    sketch_pixel<M>(words, shift, s, e, num_stamps, p, T, invT, m, G, gl, gmask, accumulate, s_tab, tl, S, n,
                     flags);
+  }
 }
 
 // Batched sketch of several frames in one persistent launch: the work list
@@ -292,8 +319,8 @@ __global__ void __launch_bounds__(kBlock) k_sketch_batch(const BatchFrame* __res
     const uint4* words = reinterpret_cast<const uint4*>(addr & ~uintptr_t(15));
     const uint32_t shift = uint32_t(addr & 15u) >> 1;
     for (uint32_t p = item.y + gid; p < item.z; p += ngroups)
-      sketch_pixel<M>(words, shift, f.offsets, f.num_stamps, p, f.T, invT, f.m, G, gl, gmask, 0, s_tab, tl, f.S,
-                      f.n, flags);
+      sketch_pixel<M>(words, shift, __ldg(f.offsets + p), __ldg(f.offsets + p + 1), f.num_stamps, p, f.T, invT, f.m,
+                      G, gl, gmask, 0, s_tab, tl, f.S, f.n, flags);
   }
 }
 
