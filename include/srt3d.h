@@ -309,6 +309,42 @@ srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t timeout_us, 
  * context stays usable. */
 srt3d_status srt3d_selftest_wait_timeout(srt3d_ctx* ctx, uint64_t wait_cycles, void* stream);
 
+/* Launch planning, host only: no device, no context, no CUDA call. Reports
+ * the shapes srt3d_sketch_stream and srt3d_reconstruct choose for a frame of
+ * rows x cols pixels with T bins, m harmonics, k_max points per pixel and
+ * APSS radius `radius`, given the device's SM count and the co-resident CTAs
+ * per SM that the persistent iteration kernel reaches (an occupancy figure the
+ * caller supplies; 2 on a GB300 at radius 1).
+ *   sketch_m, init_m     harmonic count the sketch / matched-filter kernels are
+ *                        instantiated for (the smallest instantiation >= m)
+ *   sketch_lanes         lanes per pixel of the stream sketch at the given mean
+ *                        photons per pixel (4, 8, 16 or 32)
+ *   init_grid_spacing    D of the matched filter's branch and bound: the largest
+ *                        power of two <= 64 with w_m^2 D^2 / 8 <= 0.08, w_m =
+ *                        2 pi m / T (bounds how far the matched-filter score
+ *                        can rise between two grid points)
+ *   init_grid_points     ceil(T / D), points scored per pixel and pass
+ *   tile_height, tiles   rows per 16-column tile of the one-launch iteration
+ *                        kernel and its tile (= CTA) count; 0, 0 when the frame
+ *                        runs one launch per iteration (tiles do not fit at
+ *                        once, or k_max > 2 with radius > 1)
+ * Errors: SRT3D_EINVAL for a NULL `out` or an argument outside the ranges of
+ * srt3d_reconstruct (T 2..65536, m 1..32, k_max 1..4, radius 1..3), zero
+ * rows, cols, num_sms or ctas_per_sm, or a negative or NaN photon mean. */
+typedef struct srt3d_plan_info {
+  uint32_t sketch_m;
+  uint32_t sketch_lanes;
+  uint32_t init_m;
+  uint32_t init_grid_spacing;
+  uint32_t init_grid_points;
+  uint32_t tile_height;
+  uint32_t tiles;
+} srt3d_plan_info;
+
+srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, uint32_t k_max, uint32_t radius,
+                        double mean_photons_per_pixel, uint32_t num_sms, uint32_t ctas_per_sm,
+                        srt3d_plan_info* out);
+
 srt3d_status srt3d_profile_enable(srt3d_ctx* ctx, int enable);
 srt3d_status srt3d_profile_read(srt3d_ctx* ctx, uint32_t kernel, double* total_ms, uint64_t* launches);
 uint32_t srt3d_kernel_count(void);

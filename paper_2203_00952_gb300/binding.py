@@ -76,6 +76,18 @@ class srt3d_frame(ctypes.Structure):
     ]
 
 
+class srt3d_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("sketch_m", ctypes.c_uint32),
+        ("sketch_lanes", ctypes.c_uint32),
+        ("init_m", ctypes.c_uint32),
+        ("init_grid_spacing", ctypes.c_uint32),
+        ("init_grid_points", ctypes.c_uint32),
+        ("tile_height", ctypes.c_uint32),
+        ("tiles", ctypes.c_uint32),
+    ]
+
+
 class SRT3DError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{msg} ({status})")
@@ -96,6 +108,8 @@ _SIGS = {
     "srt3d_last_error": (ctypes.c_char_p, [_vp]),
     "srt3d_sync": (_i32, [_vp, _vp]),
     "srt3d_selftest_wait_timeout": (_i32, [_vp, ctypes.c_uint64, _vp]),
+    "srt3d_plan": (_i32, [_u32, _u32, _u32, _u32, _u32, _u32, ctypes.c_double, _u32, _u32,
+                          ctypes.POINTER(srt3d_plan_info)]),
     "srt3d_hist_from_stream": (_i32, [_vp, _vp, _vp, _u64, _u32, _u32, _vp, _vp]),
     "srt3d_sketch_stream": (_i32, [_vp, _vp, _vp, _u64, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
     "srt3d_sketch_hist": (_i32, [_vp, _vp, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
@@ -300,6 +314,17 @@ def srt3d_kernel_name(kernel):
 def srt3d_selftest_wait_timeout(ctx, wait_cycles, stream=None, check=True):
     st = lib().srt3d_selftest_wait_timeout(ctx, int(wait_cycles), _stream(stream))
     return _check(ctx, st, "srt3d_selftest_wait_timeout") if check else st
+
+
+def srt3d_plan(rows, cols, T, m, k_max, radius, mean_photons_per_pixel, num_sms, ctas_per_sm):
+    """Launch shapes for a frame (host only, no device needed); raises
+    SRT3DError on invalid arguments."""
+    info = srt3d_plan_info()
+    st = lib().srt3d_plan(int(rows), int(cols), int(T), int(m), int(k_max), int(radius),
+                          float(mean_photons_per_pixel), int(num_sms), int(ctas_per_sm), ctypes.byref(info))
+    if st != SRT3D_OK:
+        raise SRT3DError(st, f"srt3d_plan: status {st}")
+    return {name: getattr(info, name) for name, _ in srt3d_plan_info._fields_}
 
 
 def profile_totals(ctx):

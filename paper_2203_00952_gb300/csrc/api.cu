@@ -216,3 +216,24 @@ srt3d_status srt3d_finalize(srt3d_ctx* ctx, const float* S, const uint32_t* n, u
 }
 
 }  // extern "C"
+
+extern "C" srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, uint32_t k_max,
+                                   uint32_t radius, double mean_photons_per_pixel, uint32_t num_sms,
+                                   uint32_t ctas_per_sm, srt3d_plan_info* out) {
+  using namespace srt3d;
+  if (!out || rows == 0 || cols == 0 || T < 2 || T > 65536 || m < 1 || m > 32 || k_max < 1 || k_max > 4 ||
+      radius < 1 || radius > 3 || num_sms == 0 || num_sms > 4096 || ctas_per_sm == 0 || ctas_per_sm > 64 ||
+      !(mean_photons_per_pixel >= 0.0))
+    return SRT3D_EINVAL;
+  srt3d_plan_info info{};
+  info.sketch_m = uint32_t(sketch_round_m(m));
+  info.sketch_lanes = 1u << sketch_default_glog2(mean_photons_per_pixel);
+  info.init_m = uint32_t(init_round_m(m));
+  info.init_grid_spacing = mf_grid_spacing_host(T, m);
+  info.init_grid_points = (T + info.init_grid_spacing - 1) / info.init_grid_spacing;
+  info.tile_height = plan_tile_height(k_max, radius, rows, cols, int(num_sms), int(ctas_per_sm));
+  const uint32_t tiles_x = (cols + 15u) / 16u;
+  info.tiles = info.tile_height ? tiles_x * ((rows + info.tile_height - 1) / info.tile_height) : 0u;
+  *out = info;
+  return SRT3D_OK;
+}

@@ -1425,6 +1425,15 @@ srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames
   }
 }
 
+uint32_t plan_tile_height(uint32_t k_max, uint32_t radius, uint32_t rows, uint32_t cols, int num_sms, int bps) {
+  if (k_max > 2 && radius > 1) return 0;  // such launches go one iteration at a time
+  switch (radius) {
+    case 1: return persistent_tile_height<1>(rows, cols, num_sms, bps);
+    case 2: return persistent_tile_height<2>(rows, cols, num_sms, bps);
+    default: return persistent_tile_height<3>(rows, cols, num_sms, bps);
+  }
+}
+
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
   (void)m;
   const size_t pk = size_t(P) * k_max;

@@ -73,3 +73,10 @@ def test_null_context_rejected(lib):
     assert lib.srt3d_sketch_stream(None, None, None, 0, 0, 16, 4, 0, None, None, None) == binding.SRT3D_EINVAL
     assert lib.srt3d_reconstruct(None, None, None, 1, 1, 16, 4, None, None, None, None, None, None,
                                  None) == binding.SRT3D_EINVAL
+
+
+def test_plan_info_layout():
+    # seven uint32 fields, as declared in srt3d.h
+    assert ctypes.sizeof(binding.srt3d_plan_info) == 28
+    assert [f for f, _ in binding.srt3d_plan_info._fields_] == [
+        "sketch_m", "sketch_lanes", "init_m", "init_grid_spacing", "init_grid_points", "tile_height", "tiles"]
