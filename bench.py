@@ -34,6 +34,13 @@ METRIC = "photons/s sketched + SRT3D-reconstructed (frames/s, p50/p99 frame late
 UNIT = "photons/s"
 E2E_DEPTH = 3  # frames in flight in the end-to-end throughput run
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernels on this workload, from the committed ncu captures named
+# beside them; a kernel changed since its capture must be taken out of here
+NCU_TRAFFIC = {
+    "iter_all": (6.866432e6, "profiles/k_iter_persistent_256x256_T4096_m10_K2_it30.md"),
+    "sketch_stream": (135.536896e6, "profiles/k_sketch_stream_256x256_T4096_m10.md"),
+}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -923,12 +930,17 @@ def gpu_arm(args):
         rooflines[name] = entry
     dominant = max(prof.items(), key=lambda kv: kv[1][0])[0]
     dom = rooflines[dominant]
-    traffic = None
+    traffic = NCU_TRAFFIC.get(dominant, (None, None))[0]
+    for name, entry in rooflines.items():
+        if name in NCU_TRAFFIC:
+            entry["traffic"], entry["traffic_source"] = NCU_TRAFFIC[name]
     roofline = {"kernel": dominant, "bound": dom.get("bound"), "achieved": dom.get("achieved"),
                 "peak": dom.get("peak"), "unit": dom.get("unit"), "frac": dom.get("frac"), "traffic": traffic,
                 "peak_source": "FP32/INT32 lane-instruction issue: 152 SMs x 128 lanes x 2070 MHz"
                 if dom.get("bound") == "alu" else f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                "avg_ms": dom["avg_ms"]}
+                "avg_ms": dom["avg_ms"],
+                "traffic_unit": "DRAM bytes per launch (ncu)",
+                "traffic_source": NCU_TRAFFIC.get(dominant, (None, None))[1]}
     sk = rooflines.get("sketch_stream", {})
     sk_hbm = (2 * N + 4 * (P + 1) + 8 * m * P + 4 * P) / 1e9 / (sk["avg_ms"] / 1e3) if sk else None
     out = {
