@@ -211,6 +211,83 @@ def test_gradient_matches_central_differences():
 
 # -------------------------------------------------------------- init / steps
 
+def _second_difference(f, x0, h):
+    return (f(x0 + h) - 2.0 * f(x0) + f(x0 - h)) / (h * h)
+
+
+def test_step_sizes_bound_the_curvature_of_the_loss():
+    # eta_t and eta_alpha are 1 / (Lipschitz constant of the gradient) under
+    # alpha <= 1 and |z_l| <= 1: the second derivative of the per-pixel loss
+    # in t_k, and the largest eigenvalue of its Hessian in alpha, never exceed
+    # (n / n_max) / eta, measured by finite differences of the loss itself
+    rng = np.random.default_rng(12)
+    T, m, K = 600, 9, 3
+    hh = oracle.h_hat(synth.impulse_response(T, 3.0), m)
+    n_max = 900.0
+    eta_t, eta_a = oracle.step_sizes(hh, n_max, K, T)
+    act = np.ones((1, K), bool)
+    for _ in range(40):
+        n = np.array([rng.uniform(1.0, n_max)])
+        a = rng.dirichlet(np.ones(K + 1))[:K][None, :]
+        t = rng.uniform(0, T, size=(1, K))
+        z = rng.uniform(0, 1, size=(1, m)) * np.exp(1j * rng.uniform(0, 2 * np.pi, size=(1, m)))
+        for k in range(K):
+            def f(x, k=k):
+                tt = t.copy()
+                tt[0, k] = x
+                return oracle.sketched_loss(z, n, tt, a, act, hh, T)[0]
+            assert abs(_second_difference(f, t[0, k], 1e-3)) <= (n[0] / n_max) / eta_t * (1 + 1e-4)
+        Hm = np.zeros((K, K))
+        for i in range(K):
+            for j in range(K):
+                def g(di, dj):
+                    aa = a.copy()
+                    aa[0, i] += di
+                    aa[0, j] += dj
+                    return oracle.sketched_loss(z, n, t, aa, act, hh, T)[0]
+                e = 1e-3
+                Hm[i, j] = (g(e, e) - g(e, -e) - g(-e, e) + g(-e, -e)) / (4 * e * e)
+        assert np.max(np.linalg.eigvalsh(Hm)) <= (n[0] / n_max) / eta_a * (1 + 1e-6)
+
+
+def test_step_sizes_are_tight_for_a_delta_pulse():
+    # the bounds are the suprema the derivation takes, over alpha <= 1 and
+    # |r| <= 2: with |hhat_l| = 1, alpha = 1 and the residual r = 2 Psi (z =
+    # 3 Psi) give d2L/dt2 = 2 n sum w_l^2 (1 + 2); K equal depths give the
+    # alpha Hessian 2 n sum |hhat|^2 times the all-ones K x K matrix. (Under
+    # |z| <= 1 the t bound is up to 3x conservative: Re(conj(r) Psi) <= 0.)
+    T, m = 256, 6
+    h = np.zeros(T)
+    h[0] = 1.0
+    hh = oracle.h_hat(h, m)
+    n = np.array([300.0])
+    eta_t, _ = oracle.step_sizes(hh, n[0], 1, T)
+    t0 = 77.3
+    w = 2 * np.pi * np.arange(1, m + 1) / T
+    z = 3.0 * np.exp(1j * w * t0)[None, :]
+    act1 = np.ones((1, 1), bool)
+    f = lambda x: oracle.sketched_loss(z, n, np.array([[x]]), np.ones((1, 1)), act1, hh, T)[0]  # noqa: E731
+    assert _second_difference(f, t0, 1e-3) == pytest.approx(1.0 / eta_t, rel=1e-5)
+    K = 3
+    _, eta_a = oracle.step_sizes(hh, n[0], K, T)
+    actK = np.ones((1, K), bool)
+    tK = np.full((1, K), t0)
+    a0 = np.full((1, K), 0.2)
+    z0 = np.zeros((1, m), complex)
+    Hm = np.zeros((K, K))
+    e = 1e-3
+    for i in range(K):
+        for j in range(K):
+            def g(di, dj):
+                aa = a0.copy()
+                aa[0, i] += di
+                aa[0, j] += dj
+                return oracle.sketched_loss(z0, n, tK, aa, actK, hh, T)[0]
+            Hm[i, j] = (g(e, e) - g(e, -e) - g(-e, e) + g(-e, -e)) / (4 * e * e)
+    assert np.max(np.linalg.eigvalsh(Hm)) == pytest.approx(1.0 / eta_a, rel=1e-6)
+
+
+
 def test_init_recovers_noise_free_single_surface():
     T, m = 1024, 4
     h = synth.impulse_response(T, 4.0)
