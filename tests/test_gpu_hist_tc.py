@@ -54,6 +54,29 @@ def test_fp16_split_exact_for_counts_above_2048(ctx):
     assert sketch_err(S, n, S_ref, n_ref) <= SPLIT_TOL
 
 
+@pytest.mark.parametrize("precision,tol,values", [
+    (B.SRT3D_FP16_SPLIT, SPLIT_TOL, [1, 1022, 1023, 1024, 1025, 1500, 2047, 2048, 2049, 4095, 4096, 65535]),
+    (B.SRT3D_BF16, BF16_TOL, [1, 126, 127, 128, 129, 200, 255, 256]),
+])
+def test_conversion_paths_at_their_count_limits(ctx, precision, tol, values):
+    # the converters take a bit-pattern path while every count of a thread's
+    # chunk is below 1024 (FP16) / 128 (BF16) and a rounding conversion
+    # otherwise; sparse pixels holding one boundary value each make a wrong
+    # path choice show up at full weight
+    P, T, m = 2 * len(values), 256, 8
+    y = np.zeros((P, T), np.uint16)
+    rng = np.random.default_rng(21)
+    for i, v in enumerate(values):
+        y[2 * i, int(rng.integers(0, T))] = v
+        b = int(rng.integers(0, T))
+        y[2 * i + 1, b] = v
+        y[2 * i + 1, (b + 7) % T] = 1
+    S, n = run(ctx, y, m, precision)
+    S_ref, n_ref = oracle.sketch_hist(y, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert sketch_err(S, n, S_ref, n_ref) <= tol
+
+
 @pytest.mark.parametrize("P,T,m,frac", [(1000, 4096, 32, 0.01), (300, 1024, 10, 1.0), (700, 2048, 3, 0.2)])
 def test_fp16_split_counts_above_2048_in_many_stages(ctx, P, T, m, frac):
     # big counts scattered over many tiles and pipeline stages (every stage
