@@ -79,71 +79,117 @@ def spec_and_params():
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_samples(frame_index: int, budget_s: float, count: int):
-    """Time the FP64 oracle on `count` bounded samples of the workload (each
-    about `budget_s` seconds of CPU work); each returns the extrapolated
-    full-frame throughput (photons/s) and a description."""
+def host_cores():
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_block(task):
+    """One bounded sample of the FP64 oracle on a block of rows of the frame:
+    the sketch of the block, the matched-filter init of its first p_in pixels,
+    and the iterations on the block from its (untimed) init. Returns the stage
+    times and the depth error of the result's first surface."""
     import numpy as np
 
     import oracle
     from oracle.reconstruct import Params
     from paper_2203_00952_gb300 import synth
 
+    stamps, offsets, truth, rows_sk, cols, p_in, prm, T, m, sigma, n_max = task
+    p = Params(**prm)
+    t0 = time.perf_counter()
+    hh = oracle.h_hat(synth.impulse_response(T, sigma), m)
+    S, n = oracle.sketch_stream(stamps, offsets, T, m)
+    z_blk = oracle.finalize(S, n)
+    t_sk = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.init_matched_filter(z_blk[:p_in], n[:p_in], hh, T, p)
+    t_init = time.perf_counter() - t0
+    st = oracle.init_matched_filter(z_blk, n, hh, T, p)[:3]
+    eta = oracle.step_sizes(hh, n_max, p.k_max, T)
+    t0 = time.perf_counter()
+    for _ in range(p.iters):
+        st = oracle.iterate(z_blk, n, st[0], st[1], st[2], hh, T, rows_sk, cols, p, *eta)[:3]
+    t_it = time.perf_counter() - t0
+    err = np.abs(st[0][:, 0] - truth)
+    det = st[2][:, 0].astype(bool) & (err <= 3 * sigma)
+    return dict(t_sk=t_sk, t_init=t_init, t_it=t_it, photons=int(offsets[-1]),
+                dae_bins=float(err[det].mean()) if det.any() else None, detections=float(det.mean()))
+
+
+def cpu_oracle_samples(frame_index: int, budget_s: float, count: int, workers: int = 1):
+    """Time the FP64 oracle on `count` bounded samples of the workload. A
+    sample runs `workers` processes at once (the host's cores), each on its own
+    block of rows with about `budget_s` seconds of CPU work; a worker's stage
+    times scale to the whole frame, and the frame time with all workers is the
+    slowest worker's estimate divided by their number. Each sample returns that
+    full-frame throughput (photons/s), the one-core figure, a description and
+    the oracle's depth error on the first block."""
+    import numpy as np
+
+    from paper_2203_00952_gb300 import synth
+
     spec, prm = spec_and_params()
     fr = synth.make_stream_frame(spec, synth.SEED_256x256, frame_index)
     P, T, m = spec.num_pixels, spec.T, WORKLOAD["m"]
     N = int(fr.offsets[-1])
-    n_all = np.diff(fr.offsets.astype(np.int64))
-    p = Params(iters=prm["iters"], k_max=prm["k_max"], radius=prm["radius"], apss_h=prm["apss_h"],
-               d_max=prm["d_max"], depth_scale=prm["depth_scale"], prune_alpha=prm["prune_alpha"],
-               smooth_lambda=prm["smooth_lambda"], min_sep=prm["min_sep"])
+    n_max = float(np.diff(fr.offsets.astype(np.int64)).max())
     scale = max(budget_s / 12.0, 1e-3)
     rows_sk = int(min(spec.rows, max(1, round(16 * scale))))
     p_sk = rows_sk * spec.cols
     p_in = int(min(p_sk, max(32, round(2048 * scale))))
-    out = []
-    for i in range(count):
-        r0 = (i * rows_sk) % (spec.rows - rows_sk + 1)
+    oprm = {k: prm[k] for k in ("iters", "k_max", "radius", "apss_h", "d_max", "depth_scale", "prune_alpha",
+                                "smooth_lambda", "min_sep")}
+
+    def task(j):
+        r0 = (j * rows_sk) % (spec.rows - rows_sk + 1)
         a, b = r0 * spec.cols, r0 * spec.cols + p_sk
         lo, hi = int(fr.offsets[a]), int(fr.offsets[b])
-        t0 = time.perf_counter()
-        hh = oracle.h_hat(synth.impulse_response(T, spec.sigma), m)
-        S, n = oracle.sketch_stream(fr.stamps[lo:hi], fr.offsets[a:b + 1] - fr.offsets[a], T, m)
-        z_blk = oracle.finalize(S, n)
-        t_sk = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        oracle.init_matched_filter(z_blk[:p_in], n[:p_in], hh, T, p)
-        t_init = time.perf_counter() - t0
-        # iterations on the sketched block of rows, from its (untimed) init
-        st = oracle.init_matched_filter(z_blk, n, hh, T, p)[:3]
-        eta = oracle.step_sizes(hh, n_all.max(), p.k_max, T)
-        t0 = time.perf_counter()
-        for _ in range(p.iters):
-            st = oracle.iterate(z_blk, n, st[0], st[1], st[2], hh, T, rows_sk, spec.cols, p, *eta)[:3]
-        t_it = time.perf_counter() - t0
-        t_frame = t_sk * P / p_sk + t_init * P / p_in + t_it * P / p_sk
-        desc = (f"FP64 numpy oracle, 1 thread: sketch of {p_sk} px ({hi - lo} photons), matched-filter init of "
-                f"{p_in} px, {p.iters} iterations on a {rows_sk}x{spec.cols} block; stage times scaled to the "
-                f"{P}-pixel frame ({N} photons)")
-        # depth error of the oracle's result on the block (first surface), the
-        # reference of "at fixed depth error" for the GPU's result on the same pixels
-        err = np.abs(st[0][:, 0] - fr.truth.depth[a:b, 0])
-        det = st[2][:, 0].astype(bool) & (err <= 3 * spec.sigma)
-        out.append(dict(value=N / t_frame, t_frame_s=t_frame, seconds=t_sk + t_init + t_it, sample=desc,
-                        stages=dict(sketch_s=t_sk, init_s=t_init, iters_s=t_it),
-                        block=dict(first_pixel=a, last_pixel=b, dae_bins=float(err[det].mean()) if det.any() else None,
-                                   detections=float(det.mean()))))
+        return (fr.stamps[lo:hi].copy(), (fr.offsets[a:b + 1] - fr.offsets[a]).astype(np.uint32),
+                fr.truth.depth[a:b, 0].copy(), rows_sk, spec.cols, p_in, oprm, T, m, spec.sigma, n_max), (a, b)
+
+    pool = None
+    if workers > 1:
+        import multiprocessing as mp
+
+        pool = mp.get_context("spawn").Pool(workers)
+    out = []
+    try:
+        for i in range(count):
+            tasks = [task(i * workers + j) for j in range(workers)]
+            args = [t for t, _ in tasks]
+            res = pool.map(_oracle_block, args) if pool else [_oracle_block(args[0])]
+            t_frames = [r["t_sk"] * P / p_sk + r["t_init"] * P / p_in + r["t_it"] * P / p_sk for r in res]
+            t_frame = max(t_frames) / workers
+            desc = (f"FP64 numpy oracle, {workers} process(es) x 1 thread, each on its own block: sketch of "
+                    f"{p_sk} px (~{res[0]['photons']} photons), matched-filter init of {p_in} px, {WORKLOAD['iters']} "
+                    f"iterations on a {rows_sk}x{spec.cols} block; each worker's stage times scaled to the "
+                    f"{P}-pixel frame ({N} photons), frame time = slowest worker / {workers}")
+            a, b = tasks[0][1]
+            out.append(dict(value=N / t_frame, value_one_core=N / float(np.median(t_frames)), t_frame_s=t_frame,
+                            cores=workers, sample=desc,
+                            stages=dict(sketch_s=res[0]["t_sk"], init_s=res[0]["t_init"], iters_s=res[0]["t_it"]),
+                            block=dict(first_pixel=a, last_pixel=b, dae_bins=res[0]["dae_bins"],
+                                       detections=res[0]["detections"])))
+    finally:
+        if pool:
+            pool.close()
+            pool.join()
     return out
 
 
-def run_cpu_child(budget_s: float, count: int = 1, frame_index: int = 0):
-    """Run the oracle timing in a fresh single-threaded process (a new
-    interpreter, not a fork of one that touched the GPU)."""
+def run_cpu_child(budget_s: float, count: int = 1, frame_index: int = 0, workers: int = 1):
+    """Run the oracle timing in a fresh process (a new interpreter, not a fork
+    of one that touched the GPU; its workers are spawned), one thread per
+    worker process."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", f"{budget_s}:{count}:{frame_index}"]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-child", f"{budget_s}:{count}:{frame_index}:{workers}"]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=3600)
     if r.returncode != 0:
         raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
@@ -762,8 +808,9 @@ def gpu_arm(args):
     # CPU baseline first (own single-threaded process), rank 0 at N=1 only
     cpu = oracle_block = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c = run_cpu_child(12.0)[0]
-        cpu = {"value": c["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": c["sample"]}
+        c = run_cpu_child(12.0, workers=host_cores())[0]
+        cpu = {"value": c["value"], "unit": UNIT, "cores": c["cores"], "kind": "oracle", "sample": c["sample"],
+               "value_one_core": c["value_one_core"]}
         oracle_block = c.get("block")
 
     fr = rank_frame(spec, rank)
@@ -999,7 +1046,7 @@ def reference_arm(args):
         return
     # each step times a bounded sample so that the whole run stays within minutes
     budget = max(0.3, min(12.0, 120.0 / max(1, args.steps + args.warmup)))
-    res = run_cpu_child(budget, args.warmup + args.steps)[args.warmup:]
+    res = run_cpu_child(budget, args.warmup + args.steps, workers=host_cores())[args.warmup:]
     vals = [c["value"] for c in res]
     secs = [c["t_frame_s"] for c in res]
     last = res[-1]
@@ -1022,7 +1069,8 @@ def reference_arm(args):
         "data": "synthetic (seeded generator of the Eq. 1 observation model: smooth depth map, Poisson counts, SBR, Gaussian pulse)",
         "config": {"workload": WORKLOAD_NAME, **{k: WORKLOAD[k] for k in ("rows", "cols", "T", "m", "iters",
                                                                           "k_max")}},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": last["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"], "value_one_core": last["value_one_core"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -1031,8 +1079,8 @@ def reference_arm(args):
 def main():
     args = parse_args()
     if args.cpu_child is not None:
-        budget, count, frame = args.cpu_child.split(":")
-        print(json.dumps(cpu_oracle_samples(int(frame), float(budget), int(count))), flush=True)
+        budget, count, frame, workers = args.cpu_child.split(":")
+        print(json.dumps(cpu_oracle_samples(int(frame), float(budget), int(count), int(workers))), flush=True)
         return
     if args.impl == "reference":
         reference_arm(args)
