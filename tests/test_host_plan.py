@@ -99,3 +99,17 @@ def test_invalid_arguments_are_refused(kw):
     with pytest.raises(B.SRT3DError) as ei:
         _plan(**kw)
     assert ei.value.status == B.SRT3D_EINVAL
+
+
+def test_bench_counts_the_grid_the_library_plans():
+    # bench.py's roofline counts the init's grid points with its own copy of
+    # the spacing rule; it must match what the library launches
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    for T in (64, 1024, 2048, 4096, 4613, 65536):
+        for m in (1, 4, 10, 16, 20, 32):
+            assert bench.mf_grid_spacing(T, m) == _plan(T=T, m=m)["init_grid_spacing"]
