@@ -39,8 +39,10 @@ reads the previous iterate, APSS and smoothing read the post-gradient state).
 Parity: the pieces are pinned separately (finite differences for the
 gradient, exact planes and spheres for APSS, constant fields for smoothing,
 noise-free sketches for init, the whole iteration's fixed point on a
-noise-free plane). The composition of the steps is a reading of RT3D and is
-checked against the synthetic ground truth, not against the paper.
+noise-free plane, step sizes against the loss curvature). The composition
+of the steps is a reading of RT3D and is checked against the synthetic ground
+truth, not against the paper: ``iterate`` and ``reconstruct`` are parity
+unpinned beyond those invariants.
 """
 from __future__ import annotations
 
@@ -283,7 +285,8 @@ def smooth_prune(alpha, active, nbh: Neighbourhood, params: Params):
 def iterate(z, n, t, alpha, active, hh, T: int, rows: int, cols: int, params: Params,
             eta_t: float, eta_a: float):
     """One SRT3D iteration: gradient step, then (if regularising) APSS depth
-    projection and intensity smoothing/pruning on the post-gradient state."""
+    projection and intensity smoothing/pruning on the post-gradient state.
+    Parity unpinned as a whole (a reading of RT3D); its steps are pinned."""
     t1, a1 = gradient_step(z, n, t, alpha, active, hh, T, eta_t, eta_a, params.weighting)
     if not params.regularize:
         act = active.copy()
@@ -297,7 +300,8 @@ def iterate(z, n, t, alpha, active, hh, T: int, rows: int, cols: int, params: Pa
 
 def reconstruct(z, n, rows: int, cols: int, T: int, hh, params: Params, init=None):
     """Full reconstruction: init (matched filter, or `init` = (t, alpha,
-    active)) then `params.iters` iterations. Returns (t, alpha, active, alpha0)."""
+    active)) then `params.iters` iterations. Returns (t, alpha, active, alpha0).
+    Parity unpinned as a whole (a reading of RT3D); its steps are pinned."""
     z = np.asarray(z, dtype=np.complex128)
     n = np.asarray(n)
     if init is None:
