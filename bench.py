@@ -320,7 +320,8 @@ def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
     the CUDA-core stream kernel (srt3d_sketch_stream) and the composed
     tensor-core route (device histogram, then the split-FP16 tcgen05 sketch;
     srt3d_sketch_stream_tc). Device time per call (CUDA events, L2 evicted
-    between calls) and the error of the second against the first."""
+    between calls) and the error of the second against the first. Also the
+    CUDA-core kernel at m = 1 and 4 against the HBM roofline."""
     import numpy as np
     import torch
 
@@ -356,6 +357,21 @@ def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
                         "cuda_cores_photons_per_s": N / (ms_cc / 1e3), "tensor_cores_photons_per_s": N / (ms_tc / 1e3),
                         "counts_equal": bool(torch.equal(n1, n2)), "max_diff_normalised": err}
         del S1, S2, n1, n2
+    # few harmonics: where the CUDA-core kernel's arithmetic falls below its
+    # 2 bytes per photon, it is bound by HBM (algorithmic bytes: the stamps,
+    # the offsets, the sums and the counts)
+    hbm_peak, peak_kind = load_peaks()
+    for m in (1, 4):
+        try:
+            S1 = torch.empty(P, m, 2, device=dev)
+            n1 = torch.empty(P, dtype=torch.int32, device=dev)
+            ms = timed(lambda: B.srt3d_sketch_stream(ctx, stamps, offsets, T, m, 0, S1, n1, stream))
+            gbs = (2 * N + 4 * (P + 1) + 8 * m * P + 4 * P) / (ms / 1e3) / 1e9
+            out[f"m{m}"] = {"cuda_cores_ms": ms, "cuda_cores_photons_per_s": N / (ms / 1e3), "GB_per_s": gbs,
+                            "hbm_frac": gbs / hbm_peak, "peak_source": f"MEASURED_PEAKS.json ({peak_kind})"}
+            del S1, n1
+        except Exception as exc:  # the main line must still print
+            out[f"m{m}"] = {"error": repr(exc)[:200]}
     return out
 
 
