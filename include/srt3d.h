@@ -328,6 +328,10 @@ srt3d_status srt3d_selftest_wait_timeout(srt3d_ctx* ctx, uint64_t wait_cycles, v
  *                        kernel and its tile (= CTA) count; 0, 0 when the frame
  *                        runs one launch per iteration (tiles do not fit at
  *                        once, or k_max > 2 with radius > 1)
+ *   serving_frame_bytes  device bytes such a frame holds while admitted by
+ *                        srt3d_submit (sketch state, counts, impulse response,
+ *                        results and reconstruction scratch): its charge
+ *                        against the context's HBM budget
  * Errors: SRT3D_EINVAL for a NULL `out` or an argument outside the ranges of
  * srt3d_reconstruct (T 2..65536, m 1..32, k_max 1..4, radius 1..3), zero
  * rows, cols, num_sms or ctas_per_sm, or a negative or NaN photon mean. */
@@ -339,6 +343,8 @@ typedef struct srt3d_plan_info {
   uint32_t init_grid_points;
   uint32_t tile_height;
   uint32_t tiles;
+  uint32_t reserved;    /* 0 */
+  uint64_t serving_frame_bytes;
 } srt3d_plan_info;
 
 srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, uint32_t k_max, uint32_t radius,

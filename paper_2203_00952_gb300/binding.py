@@ -85,6 +85,8 @@ class srt3d_plan_info(ctypes.Structure):
         ("init_grid_points", ctypes.c_uint32),
         ("tile_height", ctypes.c_uint32),
         ("tiles", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+        ("serving_frame_bytes", ctypes.c_uint64),
     ]
 
 
@@ -324,7 +326,7 @@ def srt3d_plan(rows, cols, T, m, k_max, radius, mean_photons_per_pixel, num_sms,
                           float(mean_photons_per_pixel), int(num_sms), int(ctas_per_sm), ctypes.byref(info))
     if st != SRT3D_OK:
         raise SRT3DError(st, f"srt3d_plan: status {st}")
-    return {name: getattr(info, name) for name, _ in srt3d_plan_info._fields_}
+    return {name: getattr(info, name) for name, _ in srt3d_plan_info._fields_ if name != "reserved"}
 
 
 def profile_totals(ctx):

@@ -234,6 +234,7 @@ extern "C" srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uin
   info.tile_height = plan_tile_height(k_max, radius, rows, cols, int(num_sms), int(ctas_per_sm));
   const uint32_t tiles_x = (cols + 15u) / 16u;
   info.tiles = info.tile_height ? tiles_x * ((rows + info.tile_height - 1) / info.tile_height) : 0u;
+  info.serving_frame_bytes = uint64_t(serving_frame_bytes(rows, cols, T, m, k_max));
   *out = info;
   return SRT3D_OK;
 }

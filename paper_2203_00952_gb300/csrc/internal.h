@@ -171,6 +171,8 @@ srt3d_status launch_init_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const
                                const srt3d_params& prm, cudaStream_t stream);
 int init_round_m(uint32_t m);
 uint32_t mf_grid_spacing_host(uint32_t T, uint32_t m);
+// Device bytes a serving frame holds while admitted (its share of the HBM budget).
+size_t serving_frame_bytes(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, uint32_t k_max);
 // Rows per tile of the persistent iteration kernel (0: one launch per iteration).
 uint32_t plan_tile_height(uint32_t k_max, uint32_t radius, uint32_t rows, uint32_t cols, int num_sms, int bps);
 srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,

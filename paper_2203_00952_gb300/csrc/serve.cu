@@ -160,6 +160,16 @@ void release_frame(srt3d_ctx* ctx, Serving* sv, Frame* f) {
 
 }  // namespace
 
+size_t serving_frame_bytes(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, uint32_t k_max) {
+  Frame probe;
+  probe.rows = rows;
+  probe.cols = cols;
+  probe.T = T;
+  probe.m = m;
+  probe.prm.k_max = k_max;
+  return frame_layout(&probe, nullptr);
+}
+
 void serving_destroy(srt3d_ctx* ctx) {
   Serving* sv = ctx->serving;
   if (!sv) return;

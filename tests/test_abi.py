@@ -76,7 +76,9 @@ def test_null_context_rejected(lib):
 
 
 def test_plan_info_layout():
-    # seven uint32 fields, as declared in srt3d.h
-    assert ctypes.sizeof(binding.srt3d_plan_info) == 28
+    # eight uint32 fields and a uint64, as declared in srt3d.h
+    assert ctypes.sizeof(binding.srt3d_plan_info) == 40
+    assert binding.srt3d_plan_info.serving_frame_bytes.offset == 32
     assert [f for f, _ in binding.srt3d_plan_info._fields_] == [
-        "sketch_m", "sketch_lanes", "init_m", "init_grid_spacing", "init_grid_points", "tile_height", "tiles"]
+        "sketch_m", "sketch_lanes", "init_m", "init_grid_spacing", "init_grid_points", "tile_height", "tiles",
+        "reserved", "serving_frame_bytes"]
