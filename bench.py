@@ -58,7 +58,7 @@ def parse_args():
     ap.add_argument("--hist-rows", type=int, default=512,
                     help="side of the square histogram frame of the histogram section (512 = the workload)")
     ap.add_argument("--only", choices=["all", "step", "hist", "serving", "batch", "surfaces", "pixelwise",
-                                       "streamtc"],
+                                       "streamtc", "table1"],
                     default="all")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--batch-steps", type=int, default=5)
@@ -372,6 +372,76 @@ def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
             del S1, n1
         except Exception as exc:  # the main line must still print
             out[f"m{m}"] = {"error": repr(exc)[:200]}
+    return out
+
+
+# ----------------------------------------------------------------- array sizes of Table 1
+TABLE1_SIZES = (141, 282, 423, 564, 705)
+
+
+def table1_section(B, ctx, dev, steps, flush):
+    """SRT3D on the array sizes of the paper's timing table (Table 1: 141^2 to
+    705^2 pixels, m = 5 and 10; head-like frames, T = 4613, one surface per
+    pixel, SBR 1, 100 photons per pixel; 30 iterations, since the table states
+    no count). Device time per frame (CUDA events, L2 evicted between frames)
+    of the reconstruction alone (init + iterations) and of the whole step
+    (sketch, finalize, reconstruct). The paper's numbers are from a laptop
+    RTX 3070: context, not a target."""
+    import numpy as np
+    import torch
+
+    from paper_2203_00952_gb300 import synth
+
+    T, sigma = 4613, 6.0
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "srt3d_table1_sizes_T4613_K1_it30_100ph_sbr1", "iters": 30, "k_max": 1,
+           "paper_ms_rtx3070_laptop": {"m5": [6, 12, 28, 55, 68], "m10": [7, 18, 35, 60, 88]}}
+    for side in TABLE1_SIZES:
+        try:
+            spec = synth.FrameSpec(rows=side, cols=side, T=T, sigma=sigma, mean_photons=100.0, sbr=1.0)
+            stamps, offsets, _ = synth.make_stream_frame_torch(spec, synth.SEED_256x256 + 11, 0, device=dev)
+            P = spec.num_pixels
+            N = int(offsets[-1].item())
+            h = torch.from_numpy(synth.impulse_response(T, sigma).astype(np.float32)).to(dev)
+            depth = torch.empty(P, 1, device=dev)
+            alpha = torch.empty(P, 1, device=dev)
+            active = torch.empty(P, 1, dtype=torch.uint8, device=dev)
+            alpha0 = torch.empty(P, device=dev)
+            prm = B.make_params(iters=30, k_max=1, d_max=6 * sigma, min_sep=3 * sigma)
+            row = {"pixels": P, "photons": N}
+            for m in (5, 10):
+                S = torch.empty(P, m, 2, device=dev)
+                n = torch.empty(P, dtype=torch.int32, device=dev)
+
+                def sketch():
+                    B.srt3d_sketch_stream(ctx, stamps, offsets, T, m, 0, S, n, stream)
+                    B.srt3d_finalize(ctx, S, n, m, S, stream)
+
+                def recon():
+                    B.srt3d_reconstruct(ctx, S, n, side, side, T, m, h, prm, depth, alpha, active, alpha0,
+                                        stream)
+
+                sketch()
+                recon()
+                ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+                for i in range(steps):
+                    flush.fill_(float(i))
+                    ev[i][0].record(stream)
+                    sketch()
+                    ev[i][1].record(stream)
+                    recon()
+                    ev[i][2].record(stream)
+                torch.cuda.synchronize(dev)
+                B.srt3d_sync(ctx, stream)
+                rec = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+                full = float(np.mean([e[0].elapsed_time(e[2]) for e in ev]))
+                row[f"m{m}"] = {"reconstruct_ms": rec, "step_ms": full, "frames_per_s": 1e3 / full}
+                del S, n
+            out[f"{side}x{side}"] = row
+            del stamps, offsets, depth, alpha, active, alpha0
+            torch.cuda.empty_cache()
+        except Exception as exc:  # the main line must still print
+            out[f"{side}x{side}"] = {"error": repr(exc)[:200]}
     return out
 
 
@@ -951,7 +1021,7 @@ def gpu_arm(args):
     h2d = fr.stamps.nbytes + fr.offsets.nbytes + h_host.nbytes
     d2h = sum(o.nbytes for o in outs if o is not None)
 
-    hist = batch = surfaces = pixelwise = stream_tc = None
+    hist = batch = surfaces = pixelwise = stream_tc = table1 = None
     if args.only in ("all", "streamtc") and rank == 0:
         stream_tc = stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, args.hist_steps, flush)
     if args.only in ("all", "hist") and rank == 0:
@@ -970,6 +1040,16 @@ def gpu_arm(args):
             serving = serving_section(B, dev, args.serving_seconds)
         except Exception as exc:  # the main line must still print
             serving = {"error": repr(exc)[:300]}
+    if args.only in ("all", "table1") and rank == 0:
+        # last, on its own context: nothing after it needs the device
+        try:
+            tctx = B.srt3d_create(local)
+            try:
+                table1 = table1_section(B, tctx, dev, 3, flush)
+            finally:
+                B.srt3d_destroy(tctx)
+        except Exception as exc:  # the main line must still print
+            table1 = {"error": repr(exc)[:300]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -1046,6 +1126,7 @@ def gpu_arm(args):
         "surfaces": surfaces,
         "pixelwise": pixelwise,
         "stream_tc": stream_tc,
+        "table1_sizes": table1,
         "serving": serving,
     }
     print(json.dumps(out), flush=True)
