@@ -63,6 +63,8 @@ def parse_args():
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--ref-sample-seconds", type=float, default=None,
+                    help="CPU seconds per worker and step of the reference arm (default: the run fits in minutes)")
     return ap.parse_args()
 
 
@@ -1143,6 +1145,8 @@ def reference_arm(args):
         return
     # each step times a bounded sample so that the whole run stays within minutes
     budget = max(0.3, min(12.0, 120.0 / max(1, args.steps + args.warmup)))
+    if args.ref_sample_seconds is not None:
+        budget = max(0.01, float(args.ref_sample_seconds))
     res = run_cpu_child(budget, args.warmup + args.steps, workers=host_cores())[args.warmup:]
     vals = [c["value"] for c in res]
     secs = [c["t_frame_s"] for c in res]
