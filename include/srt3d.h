@@ -151,7 +151,8 @@ srt3d_status srt3d_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const u
  * ((l b) mod T) / T), n[p] = sum_b y[p][b], as the product Y[P x T] F[T x 2m].
  *   hist      device, uint16 [num_pixels][T] row-major; 16-byte aligned base
  *             for the tensor-core precisions
- *   T         1..65536 (tensor-core precisions: a multiple of 64)
+ *   T         1..65536 (tensor-core precisions: a multiple of 64, and
+ *             num_pixels < 2^31)
  *   m         1..32
  *   precision SRT3D_FP32, SRT3D_FP16_SPLIT or SRT3D_BF16
  *   S, n      as for srt3d_sketch_stream (overwritten) */
@@ -164,7 +165,7 @@ srt3d_status srt3d_sketch_hist(srt3d_ctx* ctx, const uint16_t* hist, uint32_t nu
  * photons per pixel, so it is the faster route at large m or dense pixels.
  *   stamps, offsets, num_stamps, num_pixels, S, n  as for srt3d_sketch_stream
  *   (S and n are overwritten: no accumulate)
- *   T          a multiple of 64 in [64, 65536]
+ *   T          a multiple of 64 in [64, 65536]; num_pixels < 2^31
  *   m          1..32
  *   precision  SRT3D_FP16_SPLIT or SRT3D_BF16 (as for srt3d_sketch_hist)
  * The histogram (num_pixels x T uint16) lives in a context-owned device

@@ -144,6 +144,7 @@ extern "C" srt3d_status srt3d_sketch_hist(srt3d_ctx* ctx, const uint16_t* hist, 
     return launch_sketch_hist_fp32(ctx, hist, num_pixels, T, m, reinterpret_cast<float2*>(S), n, s);
   if (precision == SRT3D_FP16_SPLIT || precision == SRT3D_BF16) {
     if (T % 64 != 0) return set_error(ctx, SRT3D_EINVAL, "tensor-core precisions need T % 64 == 0");
+    if (num_pixels >= (1u << 31)) return set_error(ctx, SRT3D_EINVAL, "tensor-core precisions need num_pixels < 2^31");
     if (reinterpret_cast<uintptr_t>(hist) % 16) return set_error(ctx, SRT3D_EINVAL, "hist must be 16-byte aligned");
     return launch_sketch_hist_tc(ctx, hist, num_pixels, T, m, precision, reinterpret_cast<float2*>(S), n, s);
   }
@@ -165,6 +166,7 @@ extern "C" srt3d_status srt3d_sketch_stream_tc(srt3d_ctx* ctx, const uint16_t* s
   if (precision != SRT3D_FP16_SPLIT && precision != SRT3D_BF16)
     return set_error(ctx, SRT3D_EINVAL, "precision must be SRT3D_FP16_SPLIT or SRT3D_BF16");
   if (num_stamps >= (1ull << 32)) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32");
+  if (num_pixels >= (1u << 31)) return set_error(ctx, SRT3D_EINVAL, "num_pixels must be < 2^31");
   if (reinterpret_cast<uintptr_t>(S) % 8) return set_error(ctx, SRT3D_EINVAL, "S must be 8-byte aligned");
   if (num_pixels == 0) return SRT3D_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
