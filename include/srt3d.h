@@ -237,7 +237,9 @@ typedef struct srt3d_frame {
  * `stream`. params->init_mode must be SRT3D_INIT_MATCHED and
  * params->regularize 1. Results equal those of srt3d_sketch_stream +
  * srt3d_finalize + srt3d_reconstruct per frame up to the FP32 summation
- * order of the sketch. */
+ * order of the sketch. Errors: those of srt3d_reconstruct per frame, a NULL
+ * frame pointer, num_stamps >= 2^32 - 16 or rows * cols * m >= 2^32 in a
+ * frame (SRT3D_EINVAL). */
 srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* frames, uint32_t num_frames,
                                  const srt3d_params* params, void* stream);
 

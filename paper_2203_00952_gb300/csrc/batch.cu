@@ -122,6 +122,8 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
       return set_error(ctx, SRT3D_EINVAL, "NULL pointer in a frame");
     if (f.num_stamps >= (1ull << 32) - 16) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32 - 16");
     if (reinterpret_cast<uintptr_t>(f.z) % 8) return set_error(ctx, SRT3D_EINVAL, "z must be 8-byte aligned");
+    if (uint64_t(f.rows) * f.cols * f.m >= (1ull << 32))
+      return set_error(ctx, SRT3D_EINVAL, "rows * cols * m must be < 2^32 in a batch");
     st = get_phase_table(ctx, f.T, &tabs[i]);
     if (st != SRT3D_OK) return st;
     max_entries = std::max(max_entries, tabs[i].entries);
