@@ -36,7 +36,9 @@ def _omega(m: int, T: int) -> np.ndarray:
 
 
 def model_cf(t, alpha, active, hh, T: int) -> np.ndarray:
-    """Psi_l(theta) = sum_k alpha_k hhat_l exp(i w_l t_k) over active points.
+    """Psi_l(theta) = sum_k alpha_k hhat_l exp(i w_l t_k) over active points:
+    the characteristic function of the observation model at w_l (Sec. 2,
+    Eq. 4), with the background term exactly 0 at the harmonics.
 
     t, alpha, active: [P, K]; hh: [m]. Returns complex128 [P, m].
     """
@@ -54,7 +56,8 @@ def sketched_loss(z, n, t, alpha, active, hh, T: int) -> np.ndarray:
 
 
 def sketched_gradient(z, n, t, alpha, active, hh, T: int):
-    """Gradient of the per-pixel loss with respect to t_k and alpha_k.
+    """Gradient of the per-pixel loss n ||z - Psi||^2 (Sec. 3, Eq. 8 with
+    W = I) with respect to t_k and alpha_k.
 
     With r = z - Psi and E_kl = exp(i w_l t_k):
       dL/dt_k     = -2 n sum_l Re( conj(r_l) * i w_l alpha_k hhat_l E_kl )
@@ -111,7 +114,8 @@ def weighted_loss(z, n, t, alpha, active, hh, T: int, W) -> np.ndarray:
 
 
 def weighted_gradient(z, n, t, alpha, active, hh, T: int, W):
-    """Gradient of weighted_loss with W held fixed: with r = z - Psi and
+    """Gradient of weighted_loss (Sec. 2, Eq. 6 with W = Sigma_theta^-1 of
+    Eq. 5) with W held fixed: with r = z - Psi and
     v = W r,  dL/dtheta = -2 n Re( sum_l conj(dPsi_l/dtheta) v_l ), i.e. the
     W = I gradient of sketched_gradient with r replaced by v."""
     t = np.asarray(t, dtype=np.float64)

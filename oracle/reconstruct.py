@@ -71,7 +71,8 @@ class Params:
 
 
 def step_sizes(hh, n_max: float, k_max: int, T: int):
-    """Global step sizes (Lipschitz bounds with alpha <= 1, |r| <= 2):
+    """Global step sizes of the sketched gradient step (a reading of the RT3D
+    step that Sec. 3 adopts; Lipschitz bounds with alpha <= 1, |r| <= 2):
     eta_t = 1 / (2 n_max sum_l w_l^2 |hhat_l| (|hhat_l| + 2)),
     eta_alpha = 1 / (2 n_max k_max sum_l |hhat_l|^2)."""
     a = np.abs(np.asarray(hh))
@@ -83,7 +84,9 @@ def step_sizes(hh, n_max: float, k_max: int, T: int):
 
 
 def matched_filter_scores(v, hh, T: int, p0: int = 0, p1: int | None = None) -> np.ndarray:
-    """s[p, t] = Re sum_l conj(hhat_l) exp(-i w_l t) v[p, l] for integer t."""
+    """s[p, t] = Re sum_l conj(hhat_l) exp(-i w_l t) v[p, l] for integer t: the
+    matched filter of the sketched model (Eq. 4) against the data v, the
+    reading of the init that Sec. 3 leaves to RT3D."""
     v = np.asarray(v)[p0:p1]
     m = hh.size
     t = np.arange(T, dtype=np.int64)
@@ -107,7 +110,8 @@ def _project_simplex_cap(alpha, active):
 
 
 def init_matched_filter(z, n, hh, T: int, params: Params):
-    """Per-pixel sketched matched filter; returns t, alpha, active [P, K], alpha0 [P]."""
+    """Per-pixel sketched matched filter (the init reading; see the module
+    docstring); returns t, alpha, active [P, K], alpha0 [P]."""
     z = np.asarray(z)
     n = np.asarray(n)
     P = z.shape[0]
@@ -177,7 +181,8 @@ class Neighbourhood:
 
 
 def neighbour_weights(t, active, rows: int, cols: int, params: Params) -> Neighbourhood:
-    """APSS neighbourhood of every point (see module docstring)."""
+    """APSS neighbourhood of every point (the point-cloud denoiser of RT3D that
+    Sec. 3 plugs in; Guennebaud & Gross 2007 weights; see module docstring)."""
     P, K = t.shape
     rr, cc = np.divmod(np.arange(P), cols)
     r = params.radius
@@ -208,7 +213,7 @@ def neighbour_weights(t, active, rows: int, cols: int, params: Params) -> Neighb
 
 def plane_normals(nbh: Neighbourhood, active) -> np.ndarray:
     """Unit normals [P, K, 3] from a weighted least-squares plane
-    z = a + b x + c y over each point's neighbours."""
+    z = a + b x + c y over each point's neighbours (APSS reading, Sec. 3)."""
     w = nbh.w
     x = nbh.dx[:, None, None]
     y = nbh.dy[:, None, None]
@@ -233,7 +238,8 @@ def plane_normals(nbh: Neighbourhood, active) -> np.ndarray:
 
 
 def apss_depth(t, active, normals, nbh: Neighbourhood, params: Params):
-    """Depth projection onto the locally fitted algebraic sphere."""
+    """Depth projection onto the locally fitted algebraic sphere (APSS,
+    Guennebaud & Gross 2007; the depth denoiser reading of Sec. 3)."""
     w = nbh.w
     x = np.broadcast_to(nbh.dx[:, None, None], w.shape)
     y = np.broadcast_to(nbh.dy[:, None, None], w.shape)
@@ -269,7 +275,8 @@ def apss_depth(t, active, normals, nbh: Neighbourhood, params: Params):
 
 
 def smooth_prune(alpha, active, nbh: Neighbourhood, params: Params):
-    """Intensity smoothing over the APSS neighbourhood, pruning, alpha_0."""
+    """Intensity smoothing over the APSS neighbourhood, pruning, alpha_0 (the
+    intensity step reading of Sec. 3; alpha_0 = 1 - sum alpha as in Eq. 1)."""
     w = nbh.w
     a_nb = alpha[nbh.nb, nbh.kk[:, None]][:, :, None]  # [S, P, 1]
     Sw = w.sum(0)

@@ -18,7 +18,8 @@ _PIXEL_BLOCK = 2048
 
 
 def phase_indices(stamps, T: int, m: int) -> np.ndarray:
-    """k[p, l-1] = (l * x_p) mod T for l = 1..m, exact int64."""
+    """k[p, l-1] = (l * x_p) mod T for l = 1..m, exact int64: the phase index
+    of exp(i w_l x_p), w_l = 2 pi l / T, in the sketch of Sec. 2, Eq. 3."""
     x = np.asarray(stamps, dtype=np.int64)
     ell = np.arange(1, m + 1, dtype=np.int64)
     return (x[:, None] * ell[None, :]) % int(T)
@@ -38,7 +39,8 @@ def _check_stream(stamps, offsets, T):
 
 
 def sketch_stream(stamps, offsets, T: int, m: int):
-    """Unnormalised sketch state of a pixel-sorted stamp stream.
+    """Unnormalised sketch state of a pixel-sorted stamp stream (Sec. 2, Eq. 3
+    before the division by n).
 
     Returns S complex128 [P, m] (S[p, l-1] = sum over the photons of pixel p
     of exp(i 2 pi k / T), k = (l x) mod T) and n int64 [P].
