@@ -3,7 +3,7 @@
 // The paper replaces RT3D's histogram likelihood by the sketched loss
 // n ||z - Psi_theta||^2 (Eq. 6) and keeps RT3D's point-cloud prior; the
 // iteration implemented here (one reading of the cited RT3D) is, per pixel p
-// with up to K = 2 points (t_k, alpha_k):
+// with up to K = k_max <= 4 points (t_k, alpha_k):
 //   k_prep    hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau} (Eq. 4), the global
 //             step sizes, and n_max
 //   k_init    sketched matched filter (init.cu)
