@@ -444,6 +444,43 @@ def table1_section(B, ctx, dev, steps, flush):
             torch.cuda.empty_cache()
         except Exception as exc:  # the main line must still print
             out[f"{side}x{side}"] = {"error": repr(exc)[:200]}
+    # the camouflage frame's shape (32 x 32 pixels, T = 153, two surfaces in
+    # most pixels, m = 10; the paper: 12 ms for SRT3D, 20 ms for RT3D)
+    try:
+        spec = synth.FrameSpec(rows=32, cols=32, T=153, sigma=2.0, mean_photons=100.0, sbr=1.0,
+                               two_surface_frac=0.9, sep_lo=20.0, sep_hi=60.0)
+        fr = synth.make_stream_frame(spec, synth.SEED_32x32 + 11)
+        P, m, K, Tc = spec.num_pixels, 10, 2, spec.T
+        st_ = torch.from_numpy(fr.stamps.view(np.int16)).to(dev)
+        of_ = torch.from_numpy(fr.offsets.view(np.int32)).to(dev)
+        S = torch.empty(P, m, 2, device=dev)
+        n = torch.empty(P, dtype=torch.int32, device=dev)
+        depth = torch.empty(P, K, device=dev)
+        alpha = torch.empty(P, K, device=dev)
+        active = torch.empty(P, K, dtype=torch.uint8, device=dev)
+        alpha0 = torch.empty(P, device=dev)
+        h = torch.from_numpy(synth.impulse_response(Tc, spec.sigma).astype(np.float32)).to(dev)
+        prm = B.make_params(iters=30, k_max=K, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+
+        def cstep():
+            B.srt3d_sketch_stream(ctx, st_, of_, Tc, m, 0, S, n, stream)
+            B.srt3d_finalize(ctx, S, n, m, S, stream)
+            B.srt3d_reconstruct(ctx, S, n, 32, 32, Tc, m, h, prm, depth, alpha, active, alpha0, stream)
+
+        cstep()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            cstep()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        B.srt3d_sync(ctx, stream)
+        out["camouflage_32x32_T153_K2_m10"] = {"photons": int(fr.offsets[-1]),
+                                               "step_ms": float(np.mean([a.elapsed_time(b) for a, b in ev])),
+                                               "paper_ms_rtx3070_laptop": {"SRT3D": 12, "RT3D": 20}}
+    except Exception as exc:  # the main line must still print
+        out["camouflage_32x32_T153_K2_m10"] = {"error": repr(exc)[:200]}
     return out
 
 
