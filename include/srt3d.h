@@ -98,6 +98,19 @@ typedef struct srt3d_params {
                           1 = (Sigma_theta + 1e-3 I)^-1, Sigma_theta of Eq. 5 at
                           the current state, re-evaluated every iteration;
                           1 requires regularize = 0 (pixelwise estimate)      */
+  uint32_t birth_every; /* RT3D birth move (cited by Sec. 3; this library's
+                          reading: one step of orthogonal matching pursuit)
+                          after every birth_every-th iteration but the last;
+                          0 = none. Per pixel with a free slot: the residual of
+                          the least-squares fit of z by the active points at
+                          their depths, its matched filter over integer depths
+                          at least min_sep (circularly) from the nearest
+                          integer of every active depth, the argmax (smallest
+                          on ties) with its coefficient in the joint
+                          least-squares fit as intensity; born in the first
+                          free slot if that reaches prune_alpha, then the
+                          pixel's alphas are rescaled if they sum above 1.
+                          Not available in batches.                           */
 } srt3d_params;
 
 /* Create a context on CUDA device `device`. hbm_budget_bytes bounds the device
@@ -135,7 +148,16 @@ srt3d_status srt3d_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, cons
 
 /* Photon sketch of a pixel-sorted stamp stream (Sec. 2, Eq. 3, unnormalised):
  *   S[p][l-1] = sum over the photons of pixel p of exp(i 2 pi k / T),
- *   k = (l * x_p) mod T computed exactly in integers, l = 1..m;  n[p] = count.
+ *   k = (l * x_p) mod T, l = 1..m;  n[p] = count.
+ *   How the phasors are formed (a reading of Eq. 3's exact phase; the error
+ *   per term is bounded and tested): for T <= 8192 the phase of the first
+ *   harmonic, x_p itself, indexes a cos/sin table exactly; harmonics 2..m
+ *   follow the Chebyshev recurrence e_l = 2 cos(w_1 x_p) e_{l-1} - e_{l-2} in
+ *   FP32, restarted from the table at the exact integer phase (l x_p) mod T
+ *   every 8 harmonics when m > 10 (at most 3.5e-6 per term for m <= 10,
+ *   2.3e-6 with restarts). For T > 8192 the table is two-level and harmonics
+ *   come from complex rotation by e_1, resynchronised at the exact integer
+ *   phase every 16 harmonics. The sums are FP32.
  *   stamps, offsets, num_stamps, T as for srt3d_hist_from_stream
  *   m        1..32
  *   accumulate  0: overwrite S and n;  1: add into S and n (online update of
@@ -255,7 +277,13 @@ srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* frames, uint
  *   larger frames are rejected with SRT3D_EINVAL and a message.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device made current); make that first call before any
- *   stream capture.
+ *   stream capture. A device reset (cudaDeviceReset) invalidates that address
+ *   along with every context of the device: create a new context after a
+ *   reset (srt3d_create drops the cached address, and the next call through
+ *   any context looks it up again).
+ *   Each call rewrites the phase table at the array's end from host values
+ *   carried in kernel parameters (the same values srt3d_reconstruct uses, so
+ *   the results are bit for bit those of srt3d_reconstruct).
  *   All calls share the array and it keeps the last call's contents (every
  *   word is rewritten before use, nothing needs clearing): calls that overlap
  *   on the GPU (different streams or contexts of the same device) race and
@@ -292,21 +320,22 @@ srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t rows, uint
 
 /* Wait up to timeout_us for frame_id's result and copy it to host buffers
  * depth/alpha [P][k_max] float, active [P][k_max] uint8, alpha0 [P] float and
- * (if not NULL) n [P] uint32. Returns SRT3D_OK and releases the frame,
- * SRT3D_ETIMEDOUT if not done in time, SRT3D_ENOTFOUND for an unknown id, or
- * the frame's error status. */
+ * (if not NULL) n [P] uint32. Returns SRT3D_OK and releases the frame;
+ * SRT3D_ETIMEDOUT if it is not done within timeout_us (the frame stays
+ * pending; poll again); SRT3D_ENOTFOUND for an unknown id; or the frame's own
+ * device error, after which the frame is released and the outputs hold what
+ * the device produced: SRT3D_EOFFSETS / SRT3D_ERANGE for a malformed chunk,
+ * SRT3D_ETIMEDOUT when a bounded device wait of the frame's reconstruction
+ * (the grid barrier of the one-launch iteration kernel) gave up, leaving a
+ * partial result. A frame's errors are its own: other frames in flight are
+ * not affected and do not see them. */
 srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t timeout_us, float* depth,
                         float* alpha, uint8_t* active, float* alpha0, uint32_t* n);
 
-/* Measurement aid (the paper has no counterpart). With profiling enabled the
- * library brackets each of its kernel launches with CUDA events on the
- * launching stream and accumulates, per kernel, the device time and the
- * launch count. srt3d_profile_enable(ctx, 1) clears the totals and starts
- * recording, 0 stops. srt3d_profile_read() waits for the recorded events and
- * returns the totals of kernel `kernel` (an index < srt3d_kernel_count()). */
 /* Failure-detection self-test (the paper has no counterpart). Launches one
- * CTA that runs the persistent iteration kernel's bounded grid-barrier wait on
- * a barrier that nothing completes, with a limit of wait_cycles SM clock
+ * CTA that runs the persistent iteration kernel's bounded wait for a
+ * neighbour tile's progress flag on a flag that nothing raises, with a limit
+ * of wait_cycles SM clock
  * cycles (1..4e9): the wait gives up, latches the device timeout flag, and
  * the next srt3d_sync returns SRT3D_ETIMEDOUT (clearing the flag). The
  * context stays usable. */
@@ -354,6 +383,13 @@ srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, ui
                         double mean_photons_per_pixel, uint32_t num_sms, uint32_t ctas_per_sm,
                         srt3d_plan_info* out);
 
+/* Measurement aid (the paper has no counterpart). With profiling enabled the
+ * library brackets each of its kernel launches with CUDA events on the
+ * launching stream and accumulates, per kernel, the device time and the
+ * launch count. srt3d_profile_enable(ctx, 1) clears the totals and starts
+ * recording, 0 stops. srt3d_profile_read() waits for the recorded events and
+ * returns the totals of kernel `kernel` (an index < srt3d_kernel_count());
+ * srt3d_kernel_name() names it. */
 srt3d_status srt3d_profile_enable(srt3d_ctx* ctx, int enable);
 srt3d_status srt3d_profile_read(srt3d_ctx* ctx, uint32_t kernel, double* total_ms, uint64_t* launches);
 uint32_t srt3d_kernel_count(void);

@@ -46,5 +46,6 @@ from .reconstruct import (  # noqa: F401
     apss_depth,
     smooth_prune,
     iterate,
+    birth_step,
     reconstruct,
 )

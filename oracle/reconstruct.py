@@ -33,6 +33,19 @@ Each step is a plain array computation over all pixels, in float64:
   smooth alpha <- (1 - lambda) alpha + lambda sum w alpha_i / sum w with the
          same neighbours and weights; alpha < prune_alpha deactivates the
          point (alpha = 0); rescale if sum_k alpha_k > 1; alpha_0 = 1 - sum.
+  birth  (RT3D's birth move, read for the sketched loss; every `birth_every`
+         iterations, not after the last) per pixel with a free slot: the
+         residual r = z - sum_k beta_k hhat e^{i w t_k} of the least-squares
+         fit of real intensities beta to z at the active points' current
+         depths (what those points cannot explain wherever their intensities
+         sit, e.g. after smoothing), its matched filter over integer t at
+         circular distance >= min_sep from the nearest integer of every
+         active depth; t* = argmax (smallest t on ties), alpha* = the new
+         point's coefficient in the least-squares fit of z by the active
+         points and the new one (one step of orthogonal matching pursuit); if
+         alpha* >= prune_alpha a point (t*, alpha*) is born in the first free
+         slot (the other points keep their intensities); rescale if
+         sum_k alpha_k > 1.
 All points of an iteration read the state the iteration started from (grad
 reads the previous iterate, APSS and smoothing read the post-gradient state).
 
@@ -54,7 +67,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .model import SIGMA_RIDGE, sketched_gradient, weighted_gradient, weighting_matrix
+from .model import SIGMA_RIDGE, model_cf, sketched_gradient, weighted_gradient, weighting_matrix
 
 _PIXEL_BLOCK = 1024
 
@@ -71,6 +84,7 @@ class Params:
     smooth_lambda: float = 0.5
     min_sep: float = 12.0
     regularize: bool = True
+    birth_every: int = 0  # 0: no birth moves
     weighting: int = 0  # 0: W = I (SRT3D); 1: W = Sigma_theta^-1 (Eq. 6), pixelwise mode only
 
 
@@ -311,6 +325,61 @@ def iterate(z, n, t, alpha, active, hh, T: int, rows: int, cols: int, params: Pa
     return t2, a2, act2, a0
 
 
+def birth_step(z, n, t, alpha, active, hh, T: int, params: Params):
+    """RT3D birth move on the sketched loss (the reading in the module
+    docstring): per pixel with a free slot, a new point at the argmax of the
+    residual's matched filter outside the active points' exclusion zones, kept
+    if its intensity reaches prune_alpha. Returns (t, alpha, active, alpha0)."""
+    z = np.asarray(z)
+    t = np.array(t, dtype=np.float64)
+    act = np.array(active, dtype=bool)
+    a = np.where(act, np.asarray(alpha, dtype=np.float64), 0.0)
+    P, K = t.shape
+    free = ~act.all(axis=1) & (np.asarray(n) > 0)
+    if free.any():
+        idx = np.nonzero(free)[0]
+        w = 2.0 * np.pi * np.arange(1, hh.size + 1) / T
+        r = z[idx].copy()
+
+        def signatures(p, extra=None):
+            # hhat e^{i w t} of the pixel's active points (and of depth `extra`)
+            ts = list(t[p, act[p]]) + ([] if extra is None else [extra])
+            return hh[None, :] * np.exp(1j * w[None, :] * np.array(ts, dtype=np.float64)[:, None])
+
+        def fit(q, zp):
+            # real least squares: z_p ~ sum_k beta_k q_k over the 2m real equations
+            A = np.concatenate([q.real, q.imag], axis=1).T
+            return np.linalg.lstsq(A, np.concatenate([zp.real, zp.imag]), rcond=None)[0]
+
+        for j, p in enumerate(idx):
+            if act[p].any():
+                q = signatures(p)
+                r[j] = z[p] - fit(q, z[p]) @ q
+        s = matched_filter_scores(r, hh, T)
+        grid = np.arange(T)[None, :]
+        allowed = np.ones_like(s, bool)
+        for k in range(K):
+            tk = np.mod(np.floor(t[idx, k] + 0.5), T)
+            near = _circ_dist(grid, tk[:, None], T) < params.min_sep
+            allowed &= ~(near & act[idx, k][:, None])
+        s = np.where(allowed, s, -np.inf)
+        best = np.argmax(s, axis=1)
+        sb = s[np.arange(idx.size), best]
+        a_new = np.zeros(idx.size)
+        for j, p in enumerate(idx):
+            if np.isfinite(sb[j]):
+                a_new[j] = max(0.0, fit(signatures(p, float(best[j])), z[p])[-1])
+        born = a_new >= params.prune_alpha
+        slot = np.argmin(act[idx], axis=1)  # first free slot
+        for j in np.nonzero(born)[0]:
+            p, k = idx[j], slot[j]
+            t[p, k] = float(best[j])
+            a[p, k] = a_new[j]
+            act[p, k] = True
+    a = _project_simplex_cap(a, act)
+    return t, a, act, 1.0 - a.sum(axis=1)
+
+
 def reconstruct(z, n, rows: int, cols: int, T: int, hh, params: Params, init=None):
     """Full reconstruction: init (matched filter, or `init` = (t, alpha,
     active)) then `params.iters` iterations. Returns (t, alpha, active, alpha0).
@@ -325,7 +394,9 @@ def reconstruct(z, n, rows: int, cols: int, T: int, hh, params: Params, init=Non
         t, alpha, active = (np.array(a, dtype=d) for a, d in zip(init, (float, float, bool)))
         alpha0 = 1.0 - np.where(active, alpha, 0.0).sum(axis=1)
     eta_t, eta_a = step_sizes(hh, n.max(initial=0), params.k_max, T)
-    for _ in range(params.iters):
+    for it in range(params.iters):
         t, alpha, active, alpha0 = iterate(z, n, t, alpha, active, hh, T, rows, cols, params,
                                            eta_t, eta_a)
+        if params.birth_every and (it + 1) % params.birth_every == 0 and it + 1 < params.iters:
+            t, alpha, active, alpha0 = birth_step(z, n, t, alpha, active, hh, T, params)
     return t, alpha, active, alpha0

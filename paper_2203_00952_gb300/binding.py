@@ -48,13 +48,15 @@ class srt3d_params(ctypes.Structure):
         ("smooth_lambda", ctypes.c_float),
         ("min_sep", ctypes.c_float),
         ("weighting", ctypes.c_int32),
+        ("birth_every", ctypes.c_uint32),
     ]
 
 
 def make_params(iters=20, k_max=1, radius=1, init_mode=SRT3D_INIT_MATCHED, regularize=1, apss_h=2.5,
-                d_max=24.0, depth_scale=0.125, prune_alpha=0.02, smooth_lambda=0.5, min_sep=12.0, weighting=0):
+                d_max=24.0, depth_scale=0.125, prune_alpha=0.02, smooth_lambda=0.5, min_sep=12.0, weighting=0,
+                birth_every=0):
     return srt3d_params(iters, k_max, radius, init_mode, regularize, apss_h, d_max, depth_scale, prune_alpha,
-                        smooth_lambda, min_sep, weighting)
+                        smooth_lambda, min_sep, weighting, birth_every)
 
 
 class srt3d_frame(ctypes.Structure):

@@ -34,6 +34,29 @@ srt3d_status grow(srt3d_ctx* ctx, DevBuf* buf, size_t bytes) {
 }
 
 // cos/sin of 2 pi k / T in double, rounded once to float.
+uint32_t phase_table_host(uint32_t T, float2* out, bool* two_level) {
+  const double two_pi_over_T = 2.0 * M_PI / double(T);
+  if (T <= kDirectTableMax) {
+    *two_level = false;
+    for (uint32_t k = 0; k < T; ++k) {
+      double a = two_pi_over_T * double(k);
+      out[k] = make_float2(float(std::cos(a)), float(std::sin(a)));
+    }
+    return T;
+  }
+  *two_level = true;
+  const uint32_t nhi = (T + 255) / 256;
+  for (uint32_t k = 0; k < 256; ++k) {
+    double a = two_pi_over_T * double(k);
+    out[k] = make_float2(float(std::cos(a)), float(std::sin(a)));
+  }
+  for (uint32_t k = 0; k < nhi; ++k) {
+    double a = two_pi_over_T * double(256u * k);
+    out[256 + k] = make_float2(float(std::cos(a)), float(std::sin(a)));
+  }
+  return 256 + nhi;
+}
+
 srt3d_status get_phase_table(srt3d_ctx* ctx, uint32_t T, PhaseTable* out) {
   std::lock_guard<std::mutex> lock(ctx->mu);
   auto it = ctx->tables.find(T);
@@ -42,30 +65,10 @@ srt3d_status get_phase_table(srt3d_ctx* ctx, uint32_t T, PhaseTable* out) {
     return SRT3D_OK;
   }
   PhaseTable tab;
-  std::vector<float2> host;
-  const double two_pi_over_T = 2.0 * M_PI / double(T);
-  if (T <= kDirectTableMax) {
-    host.resize(T);
-    for (uint32_t k = 0; k < T; ++k) {
-      double a = two_pi_over_T * double(k);
-      host[k] = make_float2(float(std::cos(a)), float(std::sin(a)));
-    }
-  } else {
-    tab.two_level = true;
-    uint32_t nhi = (T + 255) / 256;
-    host.resize(256 + nhi);
-    for (uint32_t k = 0; k < 256; ++k) {
-      double a = two_pi_over_T * double(k);
-      host[k] = make_float2(float(std::cos(a)), float(std::sin(a)));
-    }
-    for (uint32_t k = 0; k < nhi; ++k) {
-      double a = two_pi_over_T * double(256u * k);
-      host[256 + k] = make_float2(float(std::cos(a)), float(std::sin(a)));
-    }
-  }
-  tab.entries = uint32_t(host.size());
-  SRT3D_CUDA_TRY(ctx, cudaMalloc(&tab.dev, host.size() * sizeof(float2)));
-  SRT3D_CUDA_TRY(ctx, cudaMemcpy(tab.dev, host.data(), host.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  std::vector<float2> host(kDirectTableMax);
+  tab.entries = phase_table_host(T, host.data(), &tab.two_level);
+  SRT3D_CUDA_TRY(ctx, cudaMalloc(&tab.dev, size_t(tab.entries) * sizeof(float2)));
+  SRT3D_CUDA_TRY(ctx, cudaMemcpy(tab.dev, host.data(), size_t(tab.entries) * sizeof(float2), cudaMemcpyHostToDevice));
   ctx->tables[T] = tab;
   *out = tab;
   return SRT3D_OK;
@@ -145,6 +148,12 @@ srt3d_status srt3d_create(int device, size_t hbm_budget_bytes, srt3d_ctx** out) 
     delete ctx;
     return SRT3D_ENOMEM;
   }
+  noalloc_forget_device(device);
+  if (coop_chain_init(ctx) != SRT3D_OK) {
+    cudaFree(ctx->d_flags);
+    delete ctx;
+    return SRT3D_ECUDA;
+  }
   *out = ctx;
   return SRT3D_OK;
 }
@@ -199,7 +208,7 @@ srt3d_status srt3d_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const u
   if (num_stamps >= (1ull << 32) - 16) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32 - 16");
   if (reinterpret_cast<uintptr_t>(S) % 8) return set_error(ctx, SRT3D_EINVAL, "S must be 8-byte aligned");
   if (num_pixels == 0) return SRT3D_OK;
-  return launch_sketch_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, m, accumulate,
+  return launch_sketch_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, m, accumulate ? 1 : 0,
                               reinterpret_cast<float2*>(S), n, static_cast<cudaStream_t>(stream));
 }
 

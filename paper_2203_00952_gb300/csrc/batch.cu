@@ -2,13 +2,18 @@
 // (Sec. 2, Eq. 3), normalisation and SRT3D reconstruction (Sec. 3, Eq. 8) of
 // many frames of different sizes, T, m and photon densities.
 //
-// Every stage is one persistent launch over all frames of the batch (work
-// lists of (frame, pixel range) items of about equal work for the sketch and
-// the initialisation, one CTA per tile of any frame for the iterations), and
-// the whole sequence is captured once into a CUDA graph that later calls with
-// the same frames replay. The sketch's lanes per pixel are chosen per
-// photon-density class by an autotuner that times the candidates on the
-// first frame of each class and caches the winner in the context.
+// Every stage is one launch over all frames of the batch: the sketch (one
+// launch per harmonic class, writing z = S / n directly) and the
+// initialisation (one per instantiated harmonic count) walk work lists of
+// (frame, pixel range) items of about equal work; one block per frame computes
+// hhat and the step sizes; and all iterations of all frames run in ONE
+// cooperative launch over the frames' tiles (k_iter_batch_persistent). The
+// sequence is captured once into a CUDA graph that later calls with the same
+// frames replay. Two autotuners pick launch shapes on the first call: the
+// sketch's lanes per pixel, timed per photon-density class on the first frame
+// of the class (cached in the context), and the iteration tiles' height,
+// timed on the whole batch (two iterations per candidate, after an untimed
+// sketch and init) and kept in the batch's graph.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -21,6 +26,14 @@ namespace {
 
 constexpr uint32_t kInitItemPixels = 128;
 constexpr size_t kMaxGraphs = 16;
+// Tile heights the iteration tuner times (pixels; tiles are 16 wide).
+constexpr uint32_t kTileHeights[] = {16, 12, 8};
+// Sketch work items: per CTA slot, and the largest pixel range of one item.
+constexpr uint32_t kItemsPerSlot = 4;
+constexpr double kMaxItemPixels = 2048.0;
+// Fixed sketch work of one pixel in photon equivalents (offsets, the lane
+// group's reduce-scatter of 2m sums, the stores), whatever its photon count.
+double pixel_cost(uint32_t m) { return 16.0 + 2.0 * double(m); }
 
 struct GraphEntry {
   std::vector<uint8_t> key;
@@ -106,13 +119,13 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
                                             const srt3d_params* params, void* stream_v) {
   if (!ctx) return SRT3D_EINVAL;
   if (!frames || !params || num_frames == 0) return set_error(ctx, SRT3D_EINVAL, "no frames or params");
-  if (params->init_mode != SRT3D_INIT_MATCHED || !params->regularize)
-    return set_error(ctx, SRT3D_EINVAL, "batches use the matched-filter init and the spatial prior");
+  if (params->init_mode != SRT3D_INIT_MATCHED || !params->regularize || params->birth_every)
+    return set_error(ctx, SRT3D_EINVAL, "batches use the matched-filter init and the spatial prior, no births");
   cudaStream_t stream = static_cast<cudaStream_t>(stream_v);
   // ---------------------------------------------------------------- validation, tables, tuning
   std::vector<PhaseTable> tabs(num_frames);
   std::vector<int> glog2(num_frames);
-  uint32_t max_entries = 0, max_G = 1, max_pm = 0;
+  uint32_t max_entries = 0, max_G = 1;
   for (uint32_t i = 0; i < num_frames; ++i) {
     const srt3d_frame& f = frames[i];
     srt3d_status st = validate_params(ctx, f.rows, f.cols, f.T, f.m, params);
@@ -129,7 +142,6 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     max_entries = std::max(max_entries, tabs[i].entries);
     const uint32_t D = mf_grid_spacing_host(f.T, f.m);
     max_G = std::max(max_G, (f.T + D - 1) / D);
-    max_pm = std::max(max_pm, f.rows * f.cols * f.m);
   }
   for (uint32_t i = 0; i < num_frames; ++i) {
     const srt3d_frame& f = frames[i];
@@ -172,11 +184,11 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   // ---------------------------------------------------------------- descriptors and work lists
   std::vector<BatchFrame> hf(num_frames);
   std::map<int, std::vector<uint3>> sketch_items;  // by instantiated M
-  std::map<int, uint64_t> group_photons;
+  std::map<int, double> group_cost;  // sketch work per m class, in photon equivalents
   std::map<int, std::vector<uint3>> init_items;  // by instantiated init M
-  uint32_t tiles = 0;
   for (uint32_t i = 0; i < num_frames; ++i)
-    group_photons[sketch_round_m(frames[i].m)] += frames[i].num_stamps;
+    group_cost[sketch_round_m(frames[i].m)] +=
+        double(frames[i].num_stamps) + double(frames[i].rows) * frames[i].cols * pixel_cost(frames[i].m);
   for (uint32_t i = 0; i < num_frames; ++i) {
     const srt3d_frame& f = frames[i];
     BatchFrame& b = hf[i];
@@ -201,13 +213,16 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     b.alpha0 = f.alpha0;
     b.D = mf_grid_spacing_host(f.T, f.m);
     b.tiles_x = (f.cols + 15) / 16;
-    b.tile0 = tiles;
-    tiles += b.tiles_x * ((f.rows + 15) / 16);
-    // sketch items of about equal photon counts
+    // sketch items of about equal work: photons plus a fixed cost per pixel
+    // (its offsets, the group's reduction and the stores), several items per
+    // CTA slot so that the last wave is short, and at most kMaxItemPixels
+    // pixels per item (a sparse frame must not become one CTA's work)
     const int M = sketch_round_m(f.m);
-    const double target = std::max(1.0, double(group_photons[M]) / double(ctx->num_sms * 4));
-    const double mean = std::max(1.0, double(f.num_stamps) / double(b.P));
-    const uint32_t span = uint32_t(std::min<double>(b.P, std::max(32.0, std::ceil(target / mean))));
+    const double target =
+        std::max(1.0, group_cost[M] / double(uint64_t(ctx->num_sms) * 4u * kItemsPerSlot));
+    const double per_pixel = double(f.num_stamps) / double(b.P) + pixel_cost(f.m);
+    const uint32_t span =
+        uint32_t(std::min<double>(std::min<double>(b.P, kMaxItemPixels), std::max(32.0, std::ceil(target / per_pixel))));
     for (uint32_t p0 = 0; p0 < b.P; p0 += span) sketch_items[M].push_back(make_uint3(i, p0, std::min(b.P, p0 + span)));
     for (uint32_t p0 = 0; p0 < b.P; p0 += kInitItemPixels)
       init_items[init_round_m(f.m)].push_back(make_uint3(i, p0, std::min(b.P, p0 + kInitItemPixels)));
@@ -218,10 +233,23 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   const size_t frames_bytes = al256(num_frames * sizeof(BatchFrame));
   const size_t scratch_per_frame = 512;  // hhat[32] float2 + misc[8] float
   const uint32_t K = params->k_max;
-  size_t alt_bytes = 0;  // alternate state per frame: depth, alpha (float), active (u8)
-  for (uint32_t i = 0; i < num_frames; ++i) alt_bytes += 3 * al256(size_t(hf[i].P) * K * sizeof(float));
-  const size_t bytes =
-      frames_bytes + al256(items_total * sizeof(uint3)) + num_frames * scratch_per_frame + alt_bytes;
+  size_t alt_bytes = 0;  // two exchange buffers per frame: depth, alpha (float), active (u8)
+  for (uint32_t i = 0; i < num_frames; ++i) alt_bytes += 6 * al256(size_t(hf[i].P) * K * sizeof(float));
+  // the frames' iteration tiles for a tile height (the tuner tries several)
+  const auto layout = [&](uint32_t th) {
+    uint32_t tiles = 0;
+    for (uint32_t i = 0; i < num_frames; ++i) {
+      hf[i].tile0 = tiles;
+      hf[i].tiles_y = (hf[i].rows + th - 1) / th;
+      tiles += hf[i].tiles_x * hf[i].tiles_y;
+    }
+    return tiles;
+  };
+  uint32_t max_tiles = 0;
+  for (uint32_t th : kTileHeights) max_tiles = std::max(max_tiles, layout(th));
+  const size_t flags_bytes = al256(size_t(max_tiles) * tile_flag_stride() * sizeof(unsigned));
+  const size_t bytes = frames_bytes + al256(items_total * sizeof(uint3)) + num_frames * scratch_per_frame +
+                       alt_bytes + flags_bytes;
   GraphEntry e;
   e.key = key;
   SRT3D_CUDA_TRY(ctx, cudaMalloc(&e.dmem, bytes));
@@ -235,8 +263,12 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     hf[i].depth_alt = reinterpret_cast<float*>(alt);
     hf[i].alpha_alt = reinterpret_cast<float*>(alt + pkb);
     hf[i].active_alt = reinterpret_cast<uint8_t*>(alt + 2 * pkb);
-    alt += 3 * pkb;
+    hf[i].depth_x1 = reinterpret_cast<float*>(alt + 3 * pkb);
+    hf[i].alpha_x1 = reinterpret_cast<float*>(alt + 4 * pkb);
+    hf[i].active_x1 = reinterpret_cast<uint8_t*>(alt + 5 * pkb);
+    alt += 6 * pkb;
   }
+  unsigned* tile_flags = reinterpret_cast<unsigned*>(alt);
   std::vector<uint3> all_items;
   std::vector<std::pair<int, std::pair<size_t, size_t>>> groups;  // M -> (offset, count)
   for (auto& kv : sketch_items) {
@@ -248,7 +280,6 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
     igroups.push_back({kv.first, {all_items.size(), kv.second.size()}});
     all_items.insert(all_items.end(), kv.second.begin(), kv.second.end());
   }
-  SRT3D_CUDA_TRY(ctx, cudaMemcpy(base, hf.data(), num_frames * sizeof(BatchFrame), cudaMemcpyHostToDevice));
   SRT3D_CUDA_TRY(ctx, cudaMemcpy(base + frames_bytes, all_items.data(), all_items.size() * sizeof(uint3),
                                  cudaMemcpyHostToDevice));
   const BatchFrame* d_frames = reinterpret_cast<const BatchFrame*>(base);
@@ -256,22 +287,81 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   std::vector<InitGroup> init_groups;
   for (auto& g : igroups)
     init_groups.push_back({g.first, d_items + g.second.first, uint32_t(g.second.second)});
+  const auto upload = [&](uint32_t th) {
+    const uint32_t tiles = layout(th);
+    const cudaError_t e = cudaMemcpy(base, hf.data(), num_frames * sizeof(BatchFrame), cudaMemcpyHostToDevice);
+    return e == cudaSuccess ? tiles : 0u;
+  };
+  const auto sketch_all = [&](cudaStream_t s) {
+    srt3d_status r = SRT3D_OK;
+    for (auto& g : groups)
+      if (r == SRT3D_OK)
+        r = launch_sketch_batch(ctx, d_frames, d_items + g.second.first, uint32_t(g.second.second), g.first,
+                                max_entries, s);
+    return r;
+  };
+  const bool prof_on = ctx->prof.enabled;
+  ctx->prof.enabled = false;  // neither tuning launches nor graph nodes are profiled
+  srt3d_status st = SRT3D_OK;
+  // ---------------------------------------------------------------- tile-height tuner
+  uint32_t best_th = kTileHeights[0];
+  if (params->iters > 0) {
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    float best = 1e30f;
+    st = upload(kTileHeights[0]) ? SRT3D_OK : set_error(ctx, SRT3D_ECUDA, "descriptor upload");
+    if (st == SRT3D_OK) st = sketch_all(stream);
+    srt3d_params p0 = *params;
+    p0.iters = 0;
+    if (st == SRT3D_OK)
+      st = launch_reconstruct_batch(ctx, d_frames, num_frames, init_groups.data(), uint32_t(init_groups.size()),
+                                    layout(kTileHeights[0]), kTileHeights[0], tile_flags, max_entries, max_G, p0,
+                                    stream);
+    if (st == SRT3D_OK && (cudaEventCreate(&ea) != cudaSuccess || cudaEventCreate(&eb) != cudaSuccess ||
+                           cudaStreamSynchronize(stream) != cudaSuccess))
+      st = set_error(ctx, SRT3D_ECUDA, "tuner set-up");
+    for (uint32_t th : kTileHeights) {
+      if (st != SRT3D_OK) break;
+      const uint32_t tiles = upload(th);
+      if (!tiles) {
+        st = set_error(ctx, SRT3D_ECUDA, "descriptor upload");
+        break;
+      }
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && st == SRT3D_OK; ++rep) {  // the first run warms up
+        if (cudaMemsetAsync(tile_flags, 0, flags_bytes, stream) != cudaSuccess ||
+            cudaEventRecord(ea, stream) != cudaSuccess) {
+          st = set_error(ctx, SRT3D_ECUDA, "tuner launch");
+          break;
+        }
+        st = launch_iterations_batch(ctx, d_frames, num_frames, tiles, th, tile_flags, 2, *params, stream);
+        if (st == SRT3D_OK &&
+            (cudaEventRecord(eb, stream) != cudaSuccess || cudaEventSynchronize(eb) != cudaSuccess ||
+             cudaEventElapsedTime(&ms, ea, eb) != cudaSuccess))
+          st = set_error(ctx, SRT3D_ECUDA, "tuner timing");
+      }
+      if (st == SRT3D_OK && ms < best) {
+        best = ms;
+        best_th = th;
+      }
+    }
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+  }
+  const uint32_t tiles = st == SRT3D_OK ? upload(best_th) : 0u;
+  if (st == SRT3D_OK && !tiles) st = set_error(ctx, SRT3D_ECUDA, "descriptor upload");
+  if (st != SRT3D_OK) {
+    ctx->prof.enabled = prof_on;
+    cudaFree(e.dmem);
+    return st;
+  }
   // ---------------------------------------------------------------- capture
   if (!cache->capture) SRT3D_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cache->capture, cudaStreamNonBlocking));
   cudaStream_t cs = cache->capture;
-  const bool prof_on = ctx->prof.enabled;
-  ctx->prof.enabled = false;  // no event records inside the graph
   SRT3D_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  srt3d_status st = SRT3D_OK;
-  for (auto& g : groups) {
-    if (st == SRT3D_OK)
-      st = launch_sketch_batch(ctx, d_frames, d_items + g.second.first, uint32_t(g.second.second), g.first,
-                               max_entries, cs);
-  }
-  if (st == SRT3D_OK) st = launch_finalize_batch(ctx, d_frames, num_frames, max_pm, cs);
+  st = sketch_all(cs);
   if (st == SRT3D_OK)
     st = launch_reconstruct_batch(ctx, d_frames, num_frames, init_groups.data(), uint32_t(init_groups.size()),
-                                  tiles, max_entries, max_G, *params, cs);
+                                  tiles, best_th, tile_flags, max_entries, max_G, *params, cs);
   cudaGraph_t graph = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
   ctx->prof.enabled = prof_on;

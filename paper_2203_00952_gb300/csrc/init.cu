@@ -64,12 +64,13 @@ __device__ __forceinline__ float2 mf_score2(const float2 (&cx)[M], const float2 
   return ffma2(ax, wx, fmul2(ay, nwy));
 }
 
-// Exclusion zones of a later pass: the NX earlier depths, and the least
-// circular distance min_sep a candidate keeps from each.
+// Exclusion zones of a later pass: the first `used` (<= NX) of the earlier
+// depths, and the least circular distance min_sep a candidate keeps from each.
 template <int NX>
 struct Excl {
   uint32_t t[NX > 0 ? NX : 1];
   float min_sep;
+  int used;
 };
 
 template <int NX>
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool mf_allowed(uint32_t t, const Excl<NX>& ex, uint3
 #pragma unroll
   for (int i = 0; i < NX; ++i) {
     const uint32_t d0 = t > ex.t[i] ? t - ex.t[i] : ex.t[i] - t;
-    ok = ok && float(min(d0, T - d0)) >= ex.min_sep;
+    ok = ok && (i >= ex.used || float(min(d0, T - d0)) >= ex.min_sep);
   }
   return ok;
 }
@@ -238,6 +239,7 @@ __device__ __forceinline__ void later_passes(uint32_t lane, uint32_t m, uint32_t
 #pragma unroll
     for (int i = 0; i < k; ++i) ex.t[i] = ti[i];
     ex.min_sep = min_sep;
+    ex.used = k;
     float sk;
     uint32_t tk;
     warp_argmax_scores<M, k>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, ex, &sk, &tk);
@@ -274,7 +276,7 @@ __device__ __forceinline__ void init_pixel(uint32_t p, const float2* __restrict_
   broadcast_c<M>(mine, cx, cy);
   float s1;
   uint32_t t1;
-  warp_argmax_scores<M, 0>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, Excl<0>{{0u}, 0.f}, &s1, &t1);
+  warp_argmax_scores<M, 0>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, Excl<0>{{0u}, 0.f, 0}, &s1, &t1);
   if (t1 >= T) {  // no finite score (cannot happen for finite z)
     t1 = 0u;
     s1 = 0.f;
@@ -388,6 +390,213 @@ __global__ void __launch_bounds__(kBlock, 1) k_init_batch(const BatchFrame* __re
   }
 }
 
+// Solves G x = y for the symmetric positive definite n x n system (n <= N)
+// held in the leading rows of G, by elimination without pivoting (G is a
+// Gram matrix of signatures at least min_sep apart, well conditioned).
+template <int N>
+__device__ __forceinline__ void solve_spd(float (&G)[N][N], float (&y)[N], int n) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i >= n) break;
+    const float inv = 1.f / G[i][i];
+#pragma unroll
+    for (int r = i + 1; r < N; ++r) {
+      if (r >= n) break;
+      const float f = G[r][i] * inv;
+#pragma unroll
+      for (int c = i; c < N; ++c) G[r][c] -= f * G[i][c];
+      y[r] -= f * y[i];
+    }
+  }
+#pragma unroll
+  for (int i = N - 1; i >= 0; --i) {
+    if (i >= n) continue;
+    float v = y[i];
+#pragma unroll
+    for (int c = i + 1; c < N; ++c)
+      if (c < n) v -= G[i][c] * y[c];
+    y[i] = v / G[i][i];
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// RT3D birth move on the sketched loss (a reading: RT3D's moves are cited,
+// not stated, in Sec. 3) as one step of orthogonal matching pursuit, one warp
+// per pixel with a free slot: the intensities beta of the active points are
+// fitted to z by least squares at their current depths (lane l holds harmonic
+// l's signatures hhat_l e^{i w_l t_k}, the phase of t_k from the table at its
+// integer part times the fractional part's phasor; the Gram matrix and the
+// right-hand side are warp sums), the residual's matched filter over integer
+// t at circular distance >= min_sep from the nearest integer of every active
+// depth takes its exact FP32 argmax t* (smallest t on ties) with the init's
+// branch and bound, and the new point's intensity is its coefficient in the
+// joint least-squares fit, alpha* = s(t*) / (sum |hhat|^2 - c^T G^-1 c), c_j
+// = the correlation of the new signature with point j's. A point with
+// alpha* >= prune_alpha is born in the first free slot (the others keep their
+// intensities), and the pixel is rescaled if its intensities sum above 1. The
+// state is updated in place.
+template <int K, int M>
+__global__ void __launch_bounds__(kBlock, 2) k_birth(const float2* __restrict__ z, const uint32_t* __restrict__ n,
+                                                   uint32_t P, uint32_t T, uint32_t m,
+                                                   const float2* __restrict__ table, uint32_t entries, int two_level,
+                                                   uint32_t D, const float2* __restrict__ hh_g,
+                                                   float* __restrict__ misc, float prune_alpha, float min_sep,
+                                                   float* __restrict__ depth, float* __restrict__ alpha,
+                                                   uint8_t* __restrict__ active, float* __restrict__ alpha0) {
+  extern __shared__ float2 s_tab[];
+  __shared__ float2 s_hh[kMaxM];
+  const uint32_t G = (T + D - 1u) / D;
+  float2* s_wg = s_tab + entries;
+  float* s_grid_all = reinterpret_cast<float*>(s_wg + G);
+  if (threadIdx.x < m) s_hh[threadIdx.x] = hh_g[threadIdx.x];
+  const bool tl = two_level != 0;
+  for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_tab[i] = table[i];
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) s_wg[g] = phase(s_tab, g * D, tl);
+  __syncthreads();
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const uint32_t wpb = blockDim.x >> 5;
+  const float E2 = misc[MISC_E2];
+  const float invT = 1.0f / float(T);
+  float* s_grid = s_grid_all + warp * G;
+  for (uint32_t p = blockIdx.x * wpb + warp; p < P; p += gridDim.x * wpb) {
+    float t[K], a[K];
+    bool act[K];
+    bool any_free = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      t[k] = depth[size_t(p) * K + k];
+      a[k] = alpha[size_t(p) * K + k];
+      act[k] = active[size_t(p) * K + k] != 0;
+      any_free = any_free || !act[k];
+    }
+    if (!any_free || n[p] == 0u) continue;  // uniform over the warp
+    // the active points' signatures, packed to the front (na of them)
+    const bool lv = lane < m;
+    const float2 hv = lv ? s_hh[lane] : make_float2(0.f, 0.f);
+    const float2 zl = lv ? z[size_t(p) * m + lane] : make_float2(0.f, 0.f);
+    float2 q[K];
+    int na = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      q[k] = make_float2(0.f, 0.f);
+      if (!act[k]) continue;
+      float2 qk = make_float2(0.f, 0.f);
+      if (lv) {
+        const float fl = floorf(t[k]);
+        const uint32_t ti = min(uint32_t(fl), T - 1u);
+        float sf, cf;
+        sincospif(2.f * float(lane + 1u) * (t[k] - fl) * invT, &sf, &cf);
+        qk = cmul(hv, cmul(phase(s_tab, mulmod(lane + 1u, ti, T, invT), tl), make_float2(cf, sf)));
+      }
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        if (j == na) q[j] = qk;
+      ++na;
+    }
+    // least-squares intensities at the active depths: Gram matrix and
+    // right-hand side as warp sums of Re(conj(q_j) q_k), Re(conj(q_j) z)
+    constexpr int KA = K > 1 ? K - 1 : 1;  // at most K - 1 points are active here
+    float Gm[KA][KA], beta[KA];
+#pragma unroll
+    for (int j = 0; j < KA; ++j) {
+      beta[j] = warp_sum(q[j].x * zl.x + q[j].y * zl.y);
+#pragma unroll
+      for (int k = 0; k < KA; ++k)
+        Gm[j][k] = (k >= j) ? warp_sum(q[j].x * q[k].x + q[j].y * q[k].y) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < KA; ++j)
+#pragma unroll
+      for (int k = 0; k < j; ++k) Gm[j][k] = Gm[k][j];
+    float Gc[KA][KA];
+#pragma unroll
+    for (int j = 0; j < KA; ++j)
+#pragma unroll
+      for (int k = 0; k < KA; ++k) Gc[j][k] = Gm[j][k];
+    solve_spd<KA>(Gc, beta, na);
+    float2 r = zl;
+#pragma unroll
+    for (int j = 0; j < KA; ++j)
+      if (j < na) r = make_float2(r.x - beta[j] * q[j].x, r.y - beta[j] * q[j].y);
+    const float2 mine = lv ? cmul(make_float2(hv.x, -hv.y), r) : make_float2(0.f, 0.f);
+    float2 cx[M], cy[M];
+    broadcast_c<M>(mine, cx, cy);
+    __syncwarp();
+    Excl<K> ex;
+    ex.min_sep = min_sep;
+    ex.used = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      ex.t[k] = 0u;
+      if (act[k]) {
+        uint32_t ti = uint32_t(floorf(t[k] + 0.5f));
+        ti = ti >= T ? ti - T : ti;
+#pragma unroll
+        for (int j = 0; j < K; ++j)  // compact the active depths to the front
+          if (j == ex.used) ex.t[j] = ti;
+        ++ex.used;
+      }
+    }
+    float sb;
+    uint32_t tb;
+    warp_argmax_scores<M, K>(mine, cx, cy, T, s_tab, tl, s_wg, s_grid, D, G, ex, &sb, &tb);
+    if (tb < T) {
+      // the new point's coefficient in the joint fit: s / (E2 - c^T G^-1 c)
+      const float2 qs = lv ? cmul(hv, phase(s_tab, mulmod(lane + 1u, tb, T, invT), tl)) : make_float2(0.f, 0.f);
+      float c[KA], y[KA];
+#pragma unroll
+      for (int j = 0; j < KA; ++j) y[j] = c[j] = warp_sum(q[j].x * qs.x + q[j].y * qs.y);
+#pragma unroll
+      for (int j = 0; j < KA; ++j)
+#pragma unroll
+        for (int k = 0; k < KA; ++k) Gc[j][k] = Gm[j][k];
+      solve_spd<KA>(Gc, y, na);
+      float den = E2;
+#pragma unroll
+      for (int j = 0; j < KA; ++j)
+        if (j < na) den -= c[j] * y[j];
+      const float an = den > 1e-6f * E2 ? fmaxf(0.f, sb / den) : 0.f;
+      if (an >= prune_alpha) {
+        bool placed = false;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!act[k] && !placed) {
+            t[k] = float(tb);
+            a[k] = an;
+            act[k] = true;
+            placed = true;
+          }
+        }
+      }
+    }
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) sum += act[k] ? a[k] : 0.f;
+    if (sum > 1.f) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) a[k] = a[k] / sum;
+      sum = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) sum += act[k] ? a[k] : 0.f;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        depth[size_t(p) * K + k] = t[k];
+        alpha[size_t(p) * K + k] = act[k] ? a[k] : 0.f;
+        active[size_t(p) * K + k] = act[k] ? 1 : 0;
+      }
+      alpha0[p] = 1.f - sum;
+    }
+    __syncwarp();
+  }
+}
+
 using InitFn = void (*)(const float2*, const uint32_t*, uint32_t, uint32_t, uint32_t, const float2*, uint32_t, int,
                         uint32_t, const float2*, float*, float, float, float*, float*, uint8_t*, float*);
 using InitBatchFn = void (*)(const BatchFrame*, const uint3*, uint32_t, uint32_t, uint32_t, float, float);
@@ -397,6 +606,17 @@ InitFn init_fn(int M) {
   switch (M) {
 #define CASE(k) \
   case k: return &k_init<K, k>;
+    CASE(2) CASE(4) CASE(6) CASE(8) CASE(10) CASE(12) CASE(16) CASE(20) CASE(24) CASE(32)
+#undef CASE
+    default: return nullptr;
+  }
+}
+
+template <int K>
+InitFn birth_fn(int M) {
+  switch (M) {
+#define CASE(k) \
+  case k: return &k_birth<K, k>;
     CASE(2) CASE(4) CASE(6) CASE(8) CASE(10) CASE(12) CASE(16) CASE(20) CASE(24) CASE(32)
 #undef CASE
     default: return nullptr;
@@ -447,6 +667,33 @@ srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uin
   fn<<<grid, kBlock, smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tab.two_level ? 1 : 0, D, hh, misc,
                                      prm.prune_alpha, prm.min_sep, depth, alpha, active, alpha0);
   prof_end(ctx, KID_INIT, mk, stream);
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  return SRT3D_OK;
+}
+
+srt3d_status launch_birth(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
+                          uint32_t K, const PhaseTable& tab, const float2* hh, const float* misc,
+                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
+                          cudaStream_t stream) {
+  const int M = init_round_m(m);
+  InitFn fn = K == 1 ? birth_fn<1>(M) : K == 2 ? birth_fn<2>(M) : K == 3 ? birth_fn<3>(M) : birth_fn<4>(M);
+  if (!fn) return set_error(ctx, SRT3D_EINVAL, "unsupported m");
+  const uint32_t D = mf_grid_spacing_impl(T, m);
+  const uint32_t G = (T + D - 1u) / D;
+  const size_t smem = size_t(tab.entries) * sizeof(float2) + size_t(G) * sizeof(float2) +
+                      size_t(kBlock / 32) * G * sizeof(float);
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int bps = 0;
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, kBlock, smem));
+  if (bps < 1) bps = 1;
+  const uint32_t wpb = kBlock / 32;
+  const uint64_t need = (uint64_t(P) + wpb - 1) / wpb;
+  const uint32_t grid = uint32_t(std::min<uint64_t>(need, uint64_t(ctx->num_sms) * bps));
+  const ProfMark mk = prof_begin(ctx, KID_BIRTH, stream);
+  fn<<<grid, kBlock, smem, stream>>>(z, n, P, T, m, tab.dev, tab.entries, tab.two_level ? 1 : 0, D, hh,
+                                     const_cast<float*>(misc), prm.prune_alpha, prm.min_sep, depth, alpha, active,
+                                     alpha0);
+  prof_end(ctx, KID_BIRTH, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }

@@ -60,16 +60,20 @@ struct BatchFrame {
   float* alpha0;
   float2* hh;  // per-frame reconstruction scratch: hhat [32], misc [8]
   float* misc;
-  float* depth_alt;  // alternate state buffers (the iterations ping-pong)
-  float* alpha_alt;
-  uint8_t* active_alt;
+  float* depth_alt;  // exchange buffers of the post-gradient state, alternating
+  float* alpha_alt;  // by iteration: (depth_alt, alpha_alt, active_alt) and
+  uint8_t* active_alt;  // (depth_x1, alpha_x1, active_x1)
+  float* depth_x1;
+  float* alpha_x1;
+  uint8_t* active_x1;
   uint32_t D;        // matched-filter grid spacing
   uint32_t tile0;    // first iteration tile of this frame in the batch
-  uint32_t tiles_x;  // iteration tiles per row
+  uint32_t tiles_x;  // iteration tiles per row (16 pixels wide)
+  uint32_t tiles_y;  // iteration tile rows (th pixels high)
 };
 
 // Slots of the per-frame reconstruction scalars (misc[]): step sizes, E2 =
-// sum |hhat|^2, n_max, and two words of the persistent kernel's grid barrier.
+// sum |hhat|^2, n_max, and two spare words (zeroed by the prep kernels).
 enum : uint32_t { MISC_ETA_T = 0, MISC_ETA_A = 1, MISC_E2 = 2, MISC_NMAX = 3, MISC_BAR = 4, MISC_COUNT = 8 };
 
 // Kernel ids for the profiling counters.
@@ -86,6 +90,7 @@ enum KernelId : uint32_t {
   KID_ITER_ALL,
   KID_ALPHA0,
   KID_BATCH,
+  KID_BIRTH,
   KID_COUNT
 };
 
@@ -131,6 +136,14 @@ namespace srt3d {
 srt3d_status set_error(srt3d_ctx* ctx, srt3d_status st, const std::string& msg);
 srt3d_status cuda_error(srt3d_ctx* ctx, cudaError_t err, const char* what);
 srt3d_status get_phase_table(srt3d_ctx* ctx, uint32_t T, PhaseTable* out);
+// The phase table of T in host memory (out holds kDirectTableMax entries):
+// cos/sin(2 pi k / T) in double, rounded once to float. Returns the entry
+// count; *two_level tells the layout.
+uint32_t phase_table_host(uint32_t T, float2* out, bool* two_level);
+// Drop the cached device address of the allocation-free entry point's array
+// on `device` (srt3d_create calls it, so a context created after a device
+// reset resolves the address again).
+void noalloc_forget_device(int device);
 srt3d_status grow(srt3d_ctx* ctx, DevBuf* buf, size_t bytes);
 
 // Launchers (no argument validation; callers validate).
@@ -147,24 +160,38 @@ srt3d_status launch_sketch_stream_g(srt3d_ctx* ctx, const uint16_t* stamps, cons
                                     float2* S, uint32_t* n, cudaStream_t stream, uint32_t* flags, int glog2);
 srt3d_status launch_sketch_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const uint3* d_items,
                                  uint32_t num_items, int M, uint32_t max_tab_entries, cudaStream_t stream);
-srt3d_status launch_finalize_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
-                                   uint32_t max_pm, cudaStream_t stream);
 // Init work items of one instantiated harmonic count M (see init_round_m).
 struct InitGroup {
   int M;
   const uint3* items;
   uint32_t count;
 };
+// Prep and init of every frame, then all iterations of every frame in one
+// cooperative launch over the frames' tiles (th rows high; tile_flags holds
+// total_tiles progress flags). With iters_override >= 0 that many iterations
+// run instead of prm.iters (tile-height tuning).
 srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
                                       const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
-                                      uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
-                                      cudaStream_t stream);
+                                      uint32_t th, unsigned* tile_flags, uint32_t max_tab_entries, uint32_t max_G,
+                                      const srt3d_params& prm, cudaStream_t stream);
+// The iterations alone (the frames' state is the init's or a previous run's).
+srt3d_status launch_iterations_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
+                                     uint32_t total_tiles, uint32_t th, unsigned* tile_flags, uint32_t iters,
+                                     const srt3d_params& prm, cudaStream_t stream);
+// Stride of the per-tile progress flags (words) and the largest tile height.
+uint32_t tile_flag_stride();
+uint32_t max_tile_height();
 // Matched-filter initialisation (init.cu): hh = hhat[m], misc = frame scalars
 // (misc[MISC_NMAX] receives the largest photon count, as an unsigned).
 srt3d_status launch_init(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
                          uint32_t K, const PhaseTable& tab, const float2* hh, float* misc,
                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
                          cudaStream_t stream);
+// Birth move of every pixel with a free slot (init.cu), in place.
+srt3d_status launch_birth(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t P, uint32_t T, uint32_t m,
+                          uint32_t K, const PhaseTable& tab, const float2* hh, const float* misc,
+                          const srt3d_params& prm, float* depth, float* alpha, uint8_t* active, float* alpha0,
+                          cudaStream_t stream);
 // Batched: every frame of the items has m <= M, M an instantiated count.
 srt3d_status launch_init_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, const uint3* d_items,
                                uint32_t num_items, uint32_t K, int M, uint32_t max_entries, uint32_t max_G,
@@ -181,10 +208,19 @@ srt3d_status launch_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, con
 srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows,
                               uint32_t cols, uint32_t T, uint32_t m, const float* h,
                               const srt3d_params& prm, float* depth, float* alpha, uint8_t* active,
-                              float* alpha0, void* scratch, size_t scratch_bytes, cudaStream_t stream);
+                              float* alpha0, void* scratch, size_t scratch_bytes, cudaStream_t stream,
+                              uint32_t* flags = nullptr, bool inject_barrier_timeout = false);
 size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m);
 srt3d_status validate_params(srt3d_ctx* ctx, uint32_t rows, uint32_t cols, uint32_t T, uint32_t m,
                              const srt3d_params* prm);
+
+// Cooperative launches of this library on one device run one after another:
+// each waits on a per-device event that the previous one recorded (see
+// launch_cooperative_chained in reconstruct.cu). coop_chain_init creates the
+// device's event (called by srt3d_create, with the device current).
+srt3d_status coop_chain_init(srt3d_ctx* ctx);
+srt3d_status launch_cooperative_chained(srt3d_ctx* ctx, const void* fn, dim3 grid, dim3 block, void** args,
+                                        size_t smem, cudaStream_t stream);
 
 void serving_destroy(srt3d_ctx* ctx);
 void batch_destroy(srt3d_ctx* ctx);

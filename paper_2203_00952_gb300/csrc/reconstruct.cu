@@ -19,9 +19,11 @@
 // in the persistent kernel, in registers between iterations); the
 // post-gradient state and the normals live in shared memory; hhat, the step
 // sizes and the persistent kernel's exchange buffers live in a scratch block.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
 #include <type_traits>
 #include <utility>
 
@@ -41,7 +43,15 @@ struct Scratch {
   uint8_t* act1;
   float2* hh;
   float* misc;
+  unsigned* tile_flags;  // [kMaxTileFlags] progress of each tile of the persistent kernel
 };
+
+// Words of progress flags of the persistent kernel, one flag per tile every
+// kTileFlagStride words (its own 32-byte L2 sector: flags that share a sector
+// slow the polls down); frames with more tiles than fit run one launch per
+// iteration.
+constexpr uint32_t kMaxTileFlags = 4096;
+constexpr uint32_t kTileFlagStride = 8;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -60,6 +70,8 @@ Scratch carve(void* base, uint32_t P, uint32_t K) {
   s.hh = reinterpret_cast<float2*>(p);
   p += align256(kMaxM * sizeof(float2));
   s.misc = reinterpret_cast<float*>(p);
+  p += align256(MISC_COUNT * sizeof(float));
+  s.tile_flags = reinterpret_cast<unsigned*>(p);
   return s;
 }
 
@@ -75,8 +87,10 @@ constexpr uint32_t kPrepChunk = 4096;
 __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uint32_t* __restrict__ n, uint32_t P,
                                           uint32_t T, uint32_t m, uint32_t K, const float2* __restrict__ table,
                                           uint32_t entries, int two_level, float2* __restrict__ hh_out,
-                                          float* __restrict__ misc, float2* s_tab) {
+                                          float* __restrict__ misc, float2* s_tab,
+                                          unsigned* __restrict__ tile_flags, uint32_t flag_words) {
   __shared__ float s_h[kPrepChunk];
+  for (uint32_t i = threadIdx.x; i < flag_words; i += blockDim.x) tile_flags[i] = 0u;
   __shared__ float2 s_hh[32];
   load_table(s_tab, table, entries);
   const bool tl = two_level != 0;
@@ -140,16 +154,19 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
 __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
                                                uint32_t P, uint32_t T, uint32_t m, uint32_t K,
                                                const float2* __restrict__ table, uint32_t entries, int two_level,
-                                               float2* __restrict__ hh_out, float* __restrict__ misc) {
+                                               float2* __restrict__ hh_out, float* __restrict__ misc,
+                                               unsigned* __restrict__ tile_flags) {
   extern __shared__ float2 s_tab[];
-  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, s_tab);
+  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, s_tab, tile_flags, kMaxTileFlags);
 }
 
-// Batched: one block per frame of the batch.
-__global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restrict__ frames, uint32_t K) {
+// Batched: one block per frame of the batch (each zeroes its tiles' flags).
+__global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restrict__ frames, uint32_t K,
+                                                     unsigned* __restrict__ tile_flags) {
   extern __shared__ float2 s_tab[];
   const BatchFrame& f = frames[blockIdx.x];
-  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc, s_tab);
+  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc, s_tab,
+            tile_flags + size_t(f.tile0) * kTileFlagStride, f.tiles_x * f.tiles_y * kTileFlagStride);
 }
 
 // Sketched gradient step (Jacobi) of one pixel's K points: reads the state
@@ -960,77 +977,78 @@ __global__ void __launch_bounds__(iter_threads<R>()) k_iter(Stencil st, const fl
                   active, alpha0);
 }
 
-// Batched iteration: one CTA per tile of every frame of the batch (frames
-// located by a binary search over their first tile index).
-template <int K, int R>
-__global__ void __launch_bounds__(iter_threads<R>()) k_iter_batch(Stencil base,
-                                                                  const BatchFrame* __restrict__ frames,
-                                                                  uint32_t nframes, int from_alt) {
-  uint32_t lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) / 2;
-    if (frames[mid].tile0 <= blockIdx.x)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const BatchFrame& f = frames[lo];
-  const uint32_t t = blockIdx.x - f.tile0;
-  Stencil st = base;
-  st.rows = f.rows;
-  st.cols = f.cols;
-  if (from_alt)
-    iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth_alt, f.alpha_alt,
-                    f.active_alt, f.depth, f.alpha, f.active, f.alpha0);
-  else
-    iter_tile<K, R>(st, t % f.tiles_x, t / f.tiles_x, f.S, f.n, f.T, f.m, f.hh, f.misc, f.depth, f.alpha, f.active,
-                    f.depth_alt, f.alpha_alt, f.active_alt, f.alpha0);
-}
-
 constexpr long long kGridWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+constexpr long long kInjectedWaitCycles = 100000ll;  // ~50 us: fault injection only
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident), split
-// into arrive and wait so that work needing no other CTA's data can run in
-// between. Arrivals increment a monotone counter in global memory (zeroed by
-// k_prep); the e-th barrier (e = 0, 1, ...) is complete when the counter
-// reaches (e + 1) x nblocks. The wait is bounded: after kGridWaitCycles the
-// CTA latches FLAG_DEVICE_TIMEOUT, marks itself aborted and returns false.
-__device__ __forceinline__ void grid_arrive(unsigned* bar) {
-  __syncthreads();
+// Neighbour synchronisation of the persistent kernel. Each tile has a
+// progress flag in global memory (zeroed by k_prep; one 32-byte sector per
+// flag, see kTileFlagStride): after the CTA has
+// published its post-gradient state of iteration it, it stores it + 1 to its
+// flag (release); before it reads its halo of iteration it, it waits until
+// the flag of every tile its halo touches is >= it + 1 (acquire). Only the
+// tiles within reach are waited for, not the whole grid, and the lanes of
+// warp 0 poll them in parallel (one L2 round trip per poll round). The wait is
+// bounded like the grid barrier's.
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void tile_publish(unsigned* flags, uint32_t tile, unsigned value) {
+  __syncthreads();  // every thread's state of this iteration is written
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(bar, 1u);
+    st_release(flags + tile * kTileFlagStride, value);
   }
 }
 
-__device__ __forceinline__ bool grid_wait(unsigned* bar, unsigned target, uint32_t* flags, int* s_abort,
-                                          long long limit = kGridWaitCycles) {
-  if (threadIdx.x == 0) {
-    volatile unsigned* cnt = bar;
-    const long long t0 = clock64();
-    while (*cnt < target) {
-      if (clock64() - t0 > limit) {
-        *s_abort = 1;
-        atomicOr(flags, FLAG_DEVICE_TIMEOUT);
-        break;
+// Waits for the tiles (tx + dx, ty + dy), |dx| <= 1, |dy| <= reach_y, to reach
+// `target`. Returns false (after latching FLAG_DEVICE_TIMEOUT) when a wait
+// exceeds `limit` cycles.
+__device__ __forceinline__ bool tile_wait(const unsigned* flags, int tx, int ty, int tiles_x, int tiles_y,
+                                          int reach_y, unsigned target, uint32_t* err, int* s_abort,
+                                          long long limit) {
+  if (threadIdx.x < 32) {
+    const int lane = int(threadIdx.x);
+    const int dy = lane / 3 - reach_y, dx = lane % 3 - 1;
+    const int x = tx + dx, y = ty + dy;
+    const bool mine = lane < 3 * (2 * reach_y + 1) && x >= 0 && x < tiles_x && y >= 0 && y < tiles_y;
+    bool ok = true;
+    if (mine) {
+      const unsigned* f = flags + (y * tiles_x + x) * int(kTileFlagStride);
+      const long long t0 = clock64();
+      while (ld_acquire(f) < target) {
+        if (clock64() - t0 > limit) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
       }
-      __nanosleep(32);
     }
-    __threadfence();
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0 && !ok) {
+      *s_abort = 1;
+      atomicOr(err, FLAG_DEVICE_TIMEOUT);
+    }
   }
   __syncthreads();
   return *s_abort == 0;
 }
 
-// Diagnostic: the grid barrier's bounded wait on a counter that nothing
-// increments, with a short limit (see srt3d_selftest_wait_timeout).
-__device__ unsigned g_selftest_bar = 0u;
+// Diagnostic: the persistent kernel's bounded wait on a progress flag that
+// nothing raises, with a short limit (see srt3d_selftest_wait_timeout).
+__device__ unsigned g_selftest_flag = 0u;
 
 __global__ void k_selftest_wait(uint32_t* flags, long long limit) {
   __shared__ int s_abort;
   if (threadIdx.x == 0) s_abort = 0;
   __syncthreads();
-  grid_wait(&g_selftest_bar, 1u, flags, &s_abort, limit);
+  tile_wait(&g_selftest_flag, 0, 0, 1, 1, 0, 1u, flags, &s_abort, limit);
 }
 
 // Post-gradient state of every point, exchanged between the CTAs of the
@@ -1046,17 +1064,24 @@ struct XBuf {
 // sketches and counts are loaded into shared memory once. Per iteration a
 // CTA takes the gradient step of its own pixels (pixelwise, from the state it
 // produced last iteration or the initial state), publishes the post-gradient
-// state to one of two exchange buffers, passes a grid barrier, reads its
-// halo's post-gradient state from that buffer, and runs the normals and the
-// projection stages. The buffers alternate by iteration: a CTA rewrites
-// buffer (it + 1) & 1 only after the barrier of iteration it, which every CTA
-// reaches only after reading its halo of iteration it - 1 from that buffer.
-// The final state goes to the caller's buffers after the last iteration.
+// state to one of two exchange buffers and raises its progress flag, waits for
+// the flags of the tiles its halo touches, reads the halo's post-gradient
+// state from the buffer, and runs the normals and the projection stages.
+// (Waiting only for the neighbours, each flag in its own L2 sector, is
+// slightly faster than a grid-wide barrier; overlapping the interior's stages
+// with the wait was slower, since splitting a latency-bound stage in two
+// doubles its latency.) The buffers alternate
+// by iteration: a tile rewrites buffer it & 1 at iteration it + 2 only after
+// its wait of iteration it + 1, i.e. after every tile within reach has
+// published iteration it + 1, which each does only after reading its halo of
+// iteration it from that buffer. The final state goes to the caller's
+// buffers during the last iteration.
 template <int K, int R>
 __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
-    float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags) {
+    float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags,
+    unsigned* tile_flags, uint32_t flag_base, uint32_t bar_skew, long long wait_limit) {
   using S = TileSmem<K, R>;
   constexpr int H = S::H, RW = S::RW;
   constexpr int NT = persist_threads<R>();
@@ -1083,7 +1108,8 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
   __syncthreads();
   const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
-  unsigned* bar = reinterpret_cast<unsigned*>(misc) + MISC_BAR;
+  const int tiles_y = int(gridDim.x / tiles_x);
+  const int reach_y = (H + th - 1) / th;  // tile rows the 2R halo reaches
   // the thread's own pixel (tid < npx) and its state between iterations
   const int ty = tid / kTW, tx = tid % kTW;
   const int rr = r0 + ty, cc = c0 + tx;
@@ -1095,6 +1121,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
   if (in) load_state<K>(depth, alpha, active, p, t, a, act);
   for (uint32_t it = 0; it < iters; ++it) {
     const XBuf xb = (it & 1u) ? x1 : x0;
+    const bool last = it + 1u == iters;
     // 1) gradient step of the own pixel, published for the neighbours
     if (mine) {
       grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z,
@@ -1108,8 +1135,10 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
         }
       }
     }
-    grid_arrive(bar);
-    if (!grid_wait(bar, (it + 1u) * gridDim.x, flags, &s_abort)) break;
+    tile_publish(tile_flags, blockIdx.x, flag_base + it + 1u);
+    if (!tile_wait(tile_flags, int(tile_x), int(tile_y), int(tiles_x), tiles_y, reach_y,
+                   flag_base + it + 1u + bar_skew, flags, &s_abort, wait_limit))
+      break;
     // 2) the halo's post-gradient state
     for (int j = tid; j < halo; j += NT) {
       const int i = halo_index<R>(j, th);
@@ -1134,9 +1163,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
     __syncthreads();
     float tout[K], aout[K];
     bool aact[K];
-    const bool own = stage3<K, R>(sm, st, r0, c0, th, depth, alpha, active, alpha0, tout, aout, aact,
-                                  it + 1u == iters);
-    if (own) {
+    if (stage3<K, R>(sm, st, r0, c0, th, depth, alpha, active, alpha0, tout, aout, aact, last)) {
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         t[k] = tout[k];
@@ -1148,27 +1175,123 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
   }
 }
 
-// Copy every frame's state to its alternate buffers (one CTA per tile).
-template <int K>
-__global__ void k_copy_state_batch(const BatchFrame* __restrict__ frames, uint32_t nframes) {
-  uint32_t lo = 0, hi = nframes - 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) / 2;
-    if (frames[mid].tile0 <= blockIdx.x)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  const BatchFrame& f = frames[lo];
-  const uint32_t t = blockIdx.x - f.tile0;
-  const uint32_t r = (t / f.tiles_x) * kTH + threadIdx.x / kTW, c = (t % f.tiles_x) * kTW + threadIdx.x % kTW;
-  if (r >= f.rows || c >= f.cols) return;
-  const size_t p = size_t(r) * f.cols + c;
+// All iterations of every frame of a batch in one cooperative launch. The
+// batch's tiles (16 x th pixels of any frame, numbered frame after frame) are
+// shared out round-robin over the CTAs, so a CTA owns many tiles and keeps
+// their state in global memory: the frames' own depth/alpha/active buffers,
+// updated in place. Per iteration, phase 1 takes the gradient step of every
+// own tile and publishes its post-gradient state to the frame's exchange
+// buffer of this iteration's parity, raising the tile's progress flag; phase
+// 2, for every own tile, waits for the flags of the tiles its halo touches,
+// loads the post-gradient state of tile + halo, and runs the normals and the
+// projection stages, writing the tile's new state. Phase 1 never waits, and a
+// phase-2 wait is on tiles' phase 1 of the same iteration, which the CTA that
+// is furthest behind can always complete, so the launch cannot deadlock. A
+// tile rewrites the exchange buffer of parity it & 1 in phase 1 of it + 2
+// only after its phase-2 wait of it + 1 saw every tile within reach past
+// phase 1 of it + 1, i.e. past its phase-2 reads of iteration it.
+template <int K, int R>
+__global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_batch_persistent(
+    Stencil base, const BatchFrame* __restrict__ frames, uint32_t nframes, uint32_t total_tiles, uint32_t th_u,
+    uint32_t iters, unsigned* tile_flags, uint32_t* __restrict__ err) {
+  using S = TileSmem<K, R>;
+  constexpr int H = S::H, RW = S::RW;
+  constexpr int NT = persist_threads<R>();
+  const int th = int(th_u), RH = th + 2 * H, npx = kTW * th;
+  const int reach_y = (H + th - 1) / th;
+  __shared__ S sm;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_abort = 0;
+  const int ty = tid / kTW, tx = tid % kTW;
+  uint32_t cur = 0xffffffffu;  // frame whose hhat is in shared memory
+  for (uint32_t it = 0; it < iters; ++it) {
+    // phase 1: gradient steps, published
+    for (uint32_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      uint32_t lo = 0, hi = nframes - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (frames[mid].tile0 <= tile)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const BatchFrame& f = frames[lo];
+      if (lo != cur) {
+        __syncthreads();
+        if (tid < int(f.m)) sm.hh[tid] = f.hh[tid];
+        __syncthreads();
+        cur = lo;
+      }
+      const uint32_t t = tile - f.tile0;
+      const int rr = int(t / f.tiles_x) * th + ty, cc = int(t % f.tiles_x) * kTW + tx;
+      if (tid < npx && rr < int(f.rows) && cc < int(f.cols)) {
+        const size_t p = size_t(rr) * f.cols + size_t(cc);
+        float tq[K], aq[K];
+        bool cq[K];
+        load_state<K>(f.depth, f.alpha, f.active, p, tq, aq, cq);
+        const float nmax = float(max(reinterpret_cast<const unsigned*>(f.misc)[MISC_NMAX], 1u));
+        grad_pixel<K>(f.S + p * f.m, f.n[p], f.T, f.m, sm.hh, f.misc[MISC_ETA_T] / nmax, f.misc[MISC_ETA_A] / nmax,
+                      tq, aq, cq);
+        float* xt = (it & 1u) ? f.depth_x1 : f.depth_alt;
+        float* xa = (it & 1u) ? f.alpha_x1 : f.alpha_alt;
+        uint8_t* xc = (it & 1u) ? f.active_x1 : f.active_alt;
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    f.depth_alt[p * K + k] = f.depth[p * K + k];
-    f.alpha_alt[p * K + k] = f.alpha[p * K + k];
-    f.active_alt[p * K + k] = f.active[p * K + k];
+        for (int k = 0; k < K; ++k) {
+          xt[p * K + k] = tq[k];
+          xa[p * K + k] = aq[k];
+          xc[p * K + k] = cq[k] ? 1 : 0;
+        }
+      }
+      tile_publish(tile_flags, tile, it + 1u);
+    }
+    // phase 2: normals, projection, smoothing and pruning
+    for (uint32_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      uint32_t lo = 0, hi = nframes - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) / 2;
+        if (frames[mid].tile0 <= tile)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      const BatchFrame& f = frames[lo];
+      Stencil st = base;
+      st.rows = f.rows;
+      st.cols = f.cols;
+      const uint32_t t = tile - f.tile0;
+      const int tyy = int(t / f.tiles_x), txx = int(t % f.tiles_x);
+      const int r0 = tyy * th, c0 = txx * kTW;
+      if (!tile_wait(tile_flags + size_t(f.tile0) * kTileFlagStride, txx, tyy, int(f.tiles_x), int(f.tiles_y),
+                     reach_y, it + 1u, err, &s_abort, kGridWaitCycles))
+        return;  // uniform: every thread read s_abort after the wait's barrier
+      const float* xt = (it & 1u) ? f.depth_x1 : f.depth_alt;
+      const float* xa = (it & 1u) ? f.alpha_x1 : f.alpha_alt;
+      const uint8_t* xc = (it & 1u) ? f.active_x1 : f.active_alt;
+      for (int i = tid; i < RH * RW; i += NT) {
+        const int hr = r0 - H + i / RW, hc = c0 - H + i % RW;
+        float ht[K], ha[K];
+        bool hact[K];
+        if (hr >= 0 && hr < int(f.rows) && hc >= 0 && hc < int(f.cols)) {
+          load_state<K>(xt, xa, xc, size_t(hr) * f.cols + size_t(hc), ht, ha, hact);
+        } else {
+#pragma unroll
+          for (int k = 0; k < K; ++k) {
+            ht[k] = 0.f;
+            ha[k] = 0.f;
+            hact[k] = false;
+          }
+        }
+        put_state<K, R>(sm, i, ht, ha, hact);
+      }
+      __syncthreads();
+      stage2<K, R, NT>(sm, st, th);
+      __syncthreads();
+      float tout[K], aout[K];
+      bool aact[K];
+      stage3<K, R>(sm, st, r0, c0, th, f.depth, f.alpha, f.active, f.alpha0, tout, aout, aact, true);
+      __syncthreads();  // the next tile's region load rewrites shared memory
+    }
   }
 }
 
@@ -1216,7 +1339,8 @@ uint32_t persistent_tile_height(uint32_t rows, uint32_t cols, int num_sms, int b
 template <int K, int R>
 srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const float2* z, const uint32_t* n,
                                     uint32_t T, uint32_t m, const Scratch& sc, float* depth, float* alpha,
-                                    uint8_t* active, float* alpha0, uint32_t iters, cudaStream_t stream) {
+                                    uint8_t* active, float* alpha0, uint32_t iters, uint32_t flag_base,
+                                    uint32_t* flags, bool inject_barrier_timeout, cudaStream_t stream) {
   if constexpr (K > 2 && R > 1) {
     // three or four points per pixel at radius > 1 do not fit two CTAs per SM:
     // the caller launches per iteration
@@ -1235,6 +1359,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   if (th == 0) return SRT3D_EAGAIN;
   const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
   const uint32_t ntiles = tiles_x * ((st.rows + th - 1) / th);
+  if (ntiles * kTileFlagStride > kMaxTileFlags) return SRT3D_EAGAIN;
   // exchange buffers: the scratch block's spare region and its alternate state
   const size_t pk = size_t(st.rows) * st.cols * K;
   XBuf x0{sc.xch, sc.xch + pk, reinterpret_cast<uint8_t*>(sc.xch + 2 * pk)};
@@ -1247,20 +1372,27 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   float* misc = sc.misc;
   float *d = depth, *a = alpha, *a0 = alpha0;
   uint8_t* c = active;
-  uint32_t* flags = ctx->d_flags;
-  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &x0, &x1, &it, &tx, &thv, &flags};
+  uint32_t* fl = flags;
+  // fault injection (tests): a neighbour-flag target one iteration beyond
+  // what the tiles publish, with a ~50 us limit, so every CTA's wait gives up
+  uint32_t skew = inject_barrier_timeout ? 1u : 0u, fbase = flag_base;
+  long long limit = inject_barrier_timeout ? kInjectedWaitCycles : kGridWaitCycles;
+  unsigned* tflags = sc.tile_flags;
+  void* args[] = {&stv, &zz, &nn, &TT, &mm, &hh, &misc, &d, &a, &c, &a0, &x0, &x1, &it, &tx, &thv, &fl, &tflags,
+                  &fbase, &skew, &limit};
   const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
-  SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(reinterpret_cast<void*>(fn), dim3(ntiles),
-                                                  dim3(persist_threads<R>()), args, zsmem, stream));
+  const srt3d_status ls = launch_cooperative_chained(ctx, reinterpret_cast<const void*>(fn), dim3(ntiles),
+                                                     dim3(persist_threads<R>()), args, zsmem, stream);
   prof_end(ctx, KID_ITER_ALL, mk, stream);
-  return SRT3D_OK;
+  return ls;
   }
 }
 
 template <int K>
 srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows, uint32_t cols, uint32_t T,
                  uint32_t m, const float* h, const srt3d_params& prm, float* depth, float* alpha, uint8_t* active,
-                 float* alpha0, const Scratch& sc, const PhaseTable& tab, cudaStream_t stream) {
+                 float* alpha0, const Scratch& sc, const PhaseTable& tab, uint32_t* flags, bool inject_barrier_timeout,
+                 cudaStream_t stream) {
   const uint32_t P = rows * cols;
   const size_t tab_smem = size_t(tab.entries) * sizeof(float2);
   const int tl = tab.two_level ? 1 : 0;
@@ -1268,7 +1400,8 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
-    k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc);
+    k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc,
+                                          sc.tile_flags);
     prof_end(ctx, KID_PREP, mk, stream);
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
@@ -1296,82 +1429,82 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   st.lambda = prm.smooth_lambda;
   st.prune_alpha = prm.prune_alpha;
   const dim3 tiles((cols + kTW - 1) / kTW, (rows + kTH - 1) / kTH);
-  // All iterations in one cooperative launch when every tile's CTA fits on
-  // the device at once (SRT3D_ITER_PERSISTENT=0 forces one launch per iteration).
-  if (prm.regularize && prm.iters > 0) {
-    const char* env = std::getenv("SRT3D_ITER_PERSISTENT");
-    const bool allow = !(env && env[0] == '0');
-    srt3d_status pst = SRT3D_EAGAIN;
-    if (allow) {
+  const char* env = std::getenv("SRT3D_ITER_PERSISTENT");
+  const bool allow_persistent = !(env && env[0] == '0');
+  // `count` iterations from the caller's state to the caller's state, after
+  // `done` iterations of this reconstruction (the persistent kernel's progress
+  // flags continue from there).
+  const auto iterate_span = [&](uint32_t count, uint32_t done) -> srt3d_status {
+    // All iterations in one cooperative launch when every tile's CTA fits on
+    // the device at once (SRT3D_ITER_PERSISTENT=0 forces one launch per iteration).
+    if (prm.regularize && count > 0 && allow_persistent) {
+      srt3d_status pst;
       if (prm.radius == 1)
-        pst = launch_iter_persistent<K, 1>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
-                                           stream);
+        pst = launch_iter_persistent<K, 1>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, count, done,
+                                           flags, inject_barrier_timeout, stream);
       else if (prm.radius == 2)
-        pst = launch_iter_persistent<K, 2>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
-                                           stream);
+        pst = launch_iter_persistent<K, 2>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, count, done,
+                                           flags, inject_barrier_timeout, stream);
       else
-        pst = launch_iter_persistent<K, 3>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, prm.iters,
-                                           stream);
+        pst = launch_iter_persistent<K, 3>(ctx, st, z, n, T, m, sc, depth, alpha, active, alpha0, count, done,
+                                           flags, inject_barrier_timeout, stream);
+      if (pst != SRT3D_EAGAIN) return pst;  // launched (or failed)
     }
-    if (pst != SRT3D_EAGAIN) return pst;  // launched (or failed)
-  }
-  // One launch per iteration: ping-pong between the caller's state and the
-  // scratch copy (t1, a1, act1); with an odd count the state is first copied
-  // to scratch, so that the last iteration writes the caller's buffers.
-  const size_t pk = size_t(P) * K;
-  if (prm.regularize && (prm.iters & 1u)) {
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
-    SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
-  }
-  for (uint32_t it = 0; it < prm.iters; ++it) {
-    const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);
-    const bool from_scratch = ((prm.iters - it) & 1u) != 0;  // the last iteration reads scratch
-    const float* din = from_scratch ? sc.t1 : depth;
-    const float* ain = from_scratch ? sc.a1 : alpha;
-    const uint8_t* cin = from_scratch ? sc.act1 : active;
-    float* dout = from_scratch ? depth : sc.t1;
-    float* aout = from_scratch ? alpha : sc.a1;
-    uint8_t* cout = from_scratch ? active : sc.act1;
-    if (!prm.regularize) {
-      if (prm.weighting)
-        k_grad<K, true><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
-      else
-        k_grad<K, false><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
-    } else if (prm.radius == 1) {
-      k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
-                                                           aout, cout, alpha0);
-    } else if (prm.radius == 2) {
-      k_iter<K, 2><<<tiles, iter_threads<2>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
-                                                           aout, cout, alpha0);
-    } else {
-      k_iter<K, 3><<<tiles, iter_threads<3>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
-                                                           aout, cout, alpha0);
+    // One launch per iteration: ping-pong between the caller's state and the
+    // scratch copy (t1, a1, act1); with an odd count the state is first copied
+    // to scratch, so that the last iteration writes the caller's buffers.
+    const size_t pk = size_t(P) * K;
+    if (prm.regularize && (count & 1u)) {
+      SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.t1, depth, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+      SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.a1, alpha, pk * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+      SRT3D_CUDA_TRY(ctx, cudaMemcpyAsync(sc.act1, active, pk, cudaMemcpyDeviceToDevice, stream));
     }
-    prof_end(ctx, prm.regularize ? KID_ITER : KID_GRAD, mk, stream);
-    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+    for (uint32_t it = 0; it < count; ++it) {
+      const ProfMark mk = prof_begin(ctx, prm.regularize ? KID_ITER : KID_GRAD, stream);
+      const bool from_scratch = ((count - it) & 1u) != 0;  // the last iteration reads scratch
+      const float* din = from_scratch ? sc.t1 : depth;
+      const float* ain = from_scratch ? sc.a1 : alpha;
+      const uint8_t* cin = from_scratch ? sc.act1 : active;
+      float* dout = from_scratch ? depth : sc.t1;
+      float* aout = from_scratch ? alpha : sc.a1;
+      uint8_t* cout = from_scratch ? active : sc.act1;
+      if (!prm.regularize) {
+        if (prm.weighting)
+          k_grad<K, true><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+        else
+          k_grad<K, false><<<grid, kBlock, 0, stream>>>(z, n, P, T, m, sc.hh, sc.misc, depth, alpha, active, alpha0);
+      } else if (prm.radius == 1) {
+        k_iter<K, 1><<<tiles, iter_threads<1>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                             aout, cout, alpha0);
+      } else if (prm.radius == 2) {
+        k_iter<K, 2><<<tiles, iter_threads<2>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                             aout, cout, alpha0);
+      } else {
+        k_iter<K, 3><<<tiles, iter_threads<3>(), 0, stream>>>(st, z, n, T, m, sc.hh, sc.misc, din, ain, cin, dout,
+                                                             aout, cout, alpha0);
+      }
+      prof_end(ctx, prm.regularize ? KID_ITER : KID_GRAD, mk, stream);
+      SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return SRT3D_OK;
+  };
+  if (prm.birth_every == 0) return iterate_span(prm.iters, 0);
+  // birth moves every birth_every iterations, not after the last one
+  uint32_t done = 0;
+  while (done < prm.iters) {
+    const uint32_t span = std::min(prm.birth_every, prm.iters - done);
+    srt3d_status s2 = iterate_span(span, done);
+    if (s2 != SRT3D_OK) return s2;
+    done += span;
+    if (done < prm.iters) {
+      s2 = launch_birth(ctx, z, n, P, T, m, K, tab, sc.hh, sc.misc, prm, depth, alpha, active, alpha0, stream);
+      if (s2 != SRT3D_OK) return s2;
+    }
   }
   return SRT3D_OK;
 }
 
-template <int K>
-srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const InitGroup* groups,
-                       uint32_t num_groups, uint32_t total_tiles, uint32_t max_entries, uint32_t max_G,
-                       const srt3d_params& prm, cudaStream_t stream) {
-  const size_t tab_smem = size_t(max_entries) * sizeof(float2);
-  SRT3D_CUDA_TRY(ctx,
-                 cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
-  {
-    const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
-    k_prep_batch<<<nframes, 1024, tab_smem, stream>>>(d_frames, K);
-    prof_end(ctx, KID_PREP, mk, stream);
-  }
-  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
-  for (uint32_t g = 0; g < num_groups; ++g) {
-    const srt3d_status st = launch_init_batch(ctx, d_frames, groups[g].items, groups[g].count, K, groups[g].M,
-                                              max_entries, max_G, prm, stream);
-    if (st != SRT3D_OK) return st;
-  }
+Stencil batch_stencil(const srt3d_params& prm) {
   Stencil st;
   st.rows = 0;
   st.cols = 0;
@@ -1382,47 +1515,144 @@ srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nfra
   st.ds = prm.depth_scale;
   st.lambda = prm.smooth_lambda;
   st.prune_alpha = prm.prune_alpha;
-  // ping-pong between each frame's state and its alternate buffers; with an
-  // odd count the state is first copied to the alternates (k_copy_state_batch)
-  if (prm.iters & 1u) {
-    k_copy_state_batch<K><<<total_tiles, kTW * kTH, 0, stream>>>(d_frames, nframes);
-    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  return st;
+}
+
+template <int K, int R>
+srt3d_status iterations_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, uint32_t total_tiles,
+                              uint32_t th, unsigned* tile_flags, uint32_t iters, const srt3d_params& prm,
+                              cudaStream_t stream) {
+  if (iters == 0 || total_tiles == 0) return SRT3D_OK;
+  auto fn = k_iter_batch_persistent<K, R>;
+  int bps = 0;
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, persist_threads<R>(), 0));
+  if (bps < 1) return set_error(ctx, SRT3D_ECUDA, "batched iteration kernel does not fit on an SM");
+  const uint32_t grid = std::min<uint32_t>(total_tiles, uint32_t(ctx->num_sms) * uint32_t(bps));
+  Stencil st = batch_stencil(prm);
+  const BatchFrame* fr = d_frames;
+  uint32_t nf = nframes, tt = total_tiles, thv = th, it = iters;
+  unsigned* fl = tile_flags;
+  uint32_t* err = ctx->d_flags;
+  void* args[] = {&st, &fr, &nf, &tt, &thv, &it, &fl, &err};
+  const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
+  const srt3d_status ls = launch_cooperative_chained(ctx, reinterpret_cast<const void*>(fn), dim3(grid),
+                                                     dim3(persist_threads<R>()), args, 0, stream);
+  prof_end(ctx, KID_ITER_ALL, mk, stream);
+  return ls;
+}
+
+template <int K>
+srt3d_status iterations_batch_r(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, uint32_t total_tiles,
+                                uint32_t th, unsigned* tile_flags, uint32_t iters, const srt3d_params& prm,
+                                cudaStream_t stream) {
+  if (prm.radius == 1)
+    return iterations_batch<K, 1>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+  if (prm.radius == 2)
+    return iterations_batch<K, 2>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+  return iterations_batch<K, 3>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+}
+
+template <int K>
+srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const InitGroup* groups,
+                       uint32_t num_groups, uint32_t total_tiles, uint32_t th, unsigned* tile_flags,
+                       uint32_t max_entries, uint32_t max_G, const srt3d_params& prm, cudaStream_t stream) {
+  const size_t tab_smem = size_t(max_entries) * sizeof(float2);
+  SRT3D_CUDA_TRY(ctx,
+                 cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
+  {
+    const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
+    k_prep_batch<<<nframes, 1024, tab_smem, stream>>>(d_frames, K, tile_flags);
+    prof_end(ctx, KID_PREP, mk, stream);
   }
-  for (uint32_t it = 0; it < prm.iters; ++it) {
-    const int from_alt = ((prm.iters - it) & 1u) ? 1 : 0;
-    const ProfMark mk = prof_begin(ctx, KID_ITER, stream);
-    if (prm.radius == 1)
-      k_iter_batch<K, 1><<<total_tiles, iter_threads<1>(), 0, stream>>>(st, d_frames, nframes, from_alt);
-    else if (prm.radius == 2)
-      k_iter_batch<K, 2><<<total_tiles, iter_threads<2>(), 0, stream>>>(st, d_frames, nframes, from_alt);
-    else
-      k_iter_batch<K, 3><<<total_tiles, iter_threads<3>(), 0, stream>>>(st, d_frames, nframes, from_alt);
-    prof_end(ctx, KID_ITER, mk, stream);
-    SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  for (uint32_t g = 0; g < num_groups; ++g) {
+    const srt3d_status st = launch_init_batch(ctx, d_frames, groups[g].items, groups[g].count, K, groups[g].M,
+                                              max_entries, max_G, prm, stream);
+    if (st != SRT3D_OK) return st;
   }
-  return SRT3D_OK;
+  return iterations_batch_r<K>(ctx, d_frames, nframes, total_tiles, th, tile_flags, prm.iters, prm, stream);
 }
 
 }  // namespace
 
+uint32_t tile_flag_stride() { return kTileFlagStride; }
+uint32_t max_tile_height() { return kTH; }
+
 srt3d_status launch_reconstruct_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
                                       const InitGroup* init_groups, uint32_t num_groups, uint32_t total_tiles,
-                                      uint32_t max_tab_entries, uint32_t max_G, const srt3d_params& prm,
-                                      cudaStream_t stream) {
+                                      uint32_t th, unsigned* tile_flags, uint32_t max_tab_entries, uint32_t max_G,
+                                      const srt3d_params& prm, cudaStream_t stream) {
   switch (prm.k_max) {
     case 1:
-      return run_batch<1>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                          stream);
+      return run_batch<1>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, th, tile_flags,
+                          max_tab_entries, max_G, prm, stream);
     case 2:
-      return run_batch<2>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                          stream);
+      return run_batch<2>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, th, tile_flags,
+                          max_tab_entries, max_G, prm, stream);
     case 3:
-      return run_batch<3>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                          stream);
+      return run_batch<3>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, th, tile_flags,
+                          max_tab_entries, max_G, prm, stream);
     default:
-      return run_batch<4>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, max_tab_entries, max_G, prm,
-                          stream);
+      return run_batch<4>(ctx, d_frames, nframes, init_groups, num_groups, total_tiles, th, tile_flags,
+                          max_tab_entries, max_G, prm, stream);
   }
+}
+
+srt3d_status launch_iterations_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes,
+                                     uint32_t total_tiles, uint32_t th, unsigned* tile_flags, uint32_t iters,
+                                     const srt3d_params& prm, cudaStream_t stream) {
+  switch (prm.k_max) {
+    case 1: return iterations_batch_r<1>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+    case 2: return iterations_batch_r<2>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+    case 3: return iterations_batch_r<3>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+    default: return iterations_batch_r<4>(ctx, d_frames, nframes, total_tiles, th, tile_flags, iters, prm, stream);
+  }
+}
+
+// Cooperative grids of this library never run concurrently on one device.
+// A cooperative launch is sized so that all its CTAs fit on an otherwise idle
+// device; two such grids issued from different streams (serving slots, or
+// callers' streams) could each become partly resident, every resident CTA
+// spinning in the grid barrier on CTAs that wait for the other grid's SMs,
+// until the bounded wait gives up. Chaining them through one event per device
+// (each launch waits on the event the previous launch recorded) leaves at most
+// one cooperative grid on the device; the other kernels of the library never
+// wait on anything, so the SMs they hold free up in bounded time and every CTA
+// of the cooperative grid becomes resident. Not chained while the stream is
+// being captured into a graph (an event of another stream cannot be waited on
+// there): the batch graph's cooperative node runs on the stream the caller
+// launches the graph on, serialised with that stream's work only.
+namespace {
+constexpr int kCoopMaxDevices = 64;
+std::mutex g_coop_mu;
+cudaEvent_t g_coop_ev[kCoopMaxDevices];
+}  // namespace
+
+srt3d_status coop_chain_init(srt3d_ctx* ctx) {
+  if (ctx->device < 0 || ctx->device >= kCoopMaxDevices) return SRT3D_OK;  // launches are then not chained
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop_ev[ctx->device])
+    SRT3D_CUDA_TRY(ctx, cudaEventCreateWithFlags(&g_coop_ev[ctx->device], cudaEventDisableTiming));
+  return SRT3D_OK;
+}
+
+srt3d_status launch_cooperative_chained(srt3d_ctx* ctx, const void* fn, dim3 grid, dim3 block, void** args,
+                                        size_t smem, cudaStream_t stream) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SRT3D_CUDA_TRY(ctx, cudaStreamIsCapturing(stream, &cap));
+  cudaEvent_t ev = nullptr;
+  if (cap == cudaStreamCaptureStatusNone && ctx->device >= 0 && ctx->device < kCoopMaxDevices) {
+    std::lock_guard<std::mutex> lock(g_coop_mu);
+    ev = g_coop_ev[ctx->device];
+    if (ev) {
+      SRT3D_CUDA_TRY(ctx, cudaStreamWaitEvent(stream, ev, 0));
+      SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
+      SRT3D_CUDA_TRY(ctx, cudaEventRecord(ev, stream));
+      return SRT3D_OK;
+    }
+  }
+  SRT3D_CUDA_TRY(ctx, cudaLaunchCooperativeKernel(fn, grid, block, args, smem, stream));
+  return SRT3D_OK;
 }
 
 uint32_t plan_tile_height(uint32_t k_max, uint32_t radius, uint32_t rows, uint32_t cols, int num_sms, int bps) {
@@ -1438,14 +1668,16 @@ size_t reconstruct_scratch_bytes(uint32_t P, uint32_t k_max, uint32_t m) {
   (void)m;
   const size_t pk = size_t(P) * k_max;
   return align256(pk * 16) + 2 * align256(pk * sizeof(float)) + align256(pk) +
-         align256(kMaxM * sizeof(float2)) + align256(MISC_COUNT * sizeof(float));
+         align256(kMaxM * sizeof(float2)) + align256(MISC_COUNT * sizeof(float)) +
+         align256(kMaxTileFlags * sizeof(unsigned));
 }
 
 srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t rows, uint32_t cols,
                               uint32_t T, uint32_t m, const float* h, const srt3d_params& prm, float* depth,
                               float* alpha, uint8_t* active, float* alpha0, void* scratch, size_t scratch_bytes,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, uint32_t* flags, bool inject_barrier_timeout) {
   const uint32_t P = rows * cols;
+  if (!flags) flags = ctx->d_flags;
   if (scratch_bytes < reconstruct_scratch_bytes(P, prm.k_max, m))
     return set_error(ctx, SRT3D_EINVAL, "reconstruction scratch too small");
   PhaseTable tab;
@@ -1453,10 +1685,14 @@ srt3d_status reconstruct_impl(srt3d_ctx* ctx, const float2* z, const uint32_t* n
   if (st != SRT3D_OK) return st;
   const Scratch sc = carve(scratch, P, prm.k_max);
   switch (prm.k_max) {
-    case 1: return run<1>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
-    case 2: return run<2>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
-    case 3: return run<3>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
-    default: return run<4>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, stream);
+    case 1: return run<1>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, flags,
+                            inject_barrier_timeout, stream);
+    case 2: return run<2>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, flags,
+                            inject_barrier_timeout, stream);
+    case 3: return run<3>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, flags,
+                            inject_barrier_timeout, stream);
+    default: return run<4>(ctx, z, n, rows, cols, T, m, h, prm, depth, alpha, active, alpha0, sc, tab, flags,
+                           inject_barrier_timeout, stream);
   }
 }
 
@@ -1508,18 +1744,29 @@ constexpr uint64_t kNoAllocMaxPoints = 655360;  // rows * cols * k_max
 std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
 
-// cos/sin(2 pi k / T) in double, rounded once to float: the same values the
-// host builds for the allocating path.
-__global__ void k_noalloc_phase_table(uint32_t T, uint32_t entries, int two_level, float2* __restrict__ tab) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= entries) return;
-  const double k = two_level ? (i < 256u ? double(i) : 256.0 * double(i - 256u)) : double(i);
-  double s, c;
-  sincospi(2.0 * k / double(T), &s, &c);
-  tab[i] = make_float2(float(c), float(s));
+// The phase table reaches the array through kernel parameters: each launch
+// carries up to kNoAllocTableChunk entries (24 KiB of its 32 KiB parameter
+// space) built on the host by phase_table_host, the same values the
+// allocating path uploads, so the two entry points compute bit for bit the
+// same result. No host staging, no copy from pageable memory, no device FP64.
+constexpr uint32_t kNoAllocTableChunk = 3072;
+struct TableChunk {
+  float2 v[kNoAllocTableChunk];
+};
+float2 g_noalloc_host_table[kDirectTableMax];  // guarded by g_noalloc_mu
+
+__global__ void k_noalloc_put_table(const TableChunk chunk, uint32_t first, uint32_t count, float2* __restrict__ tab) {
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) tab[first + i] = chunk.v[i];
 }
 
 }  // namespace
+
+void noalloc_forget_device(int device) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  g_noalloc_addr[device] = nullptr;
+}
+
 }  // namespace srt3d
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[srt3d::kNoAllocBytes];
@@ -1561,21 +1808,34 @@ extern "C" srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z
     base = g_noalloc_addr[ctx->device];
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // Phase table at the end of the array, rebuilt on every call (every word of
-  // the array is written before it is read within a call; nothing needs clearing).
+  // Phase table at the end of the array, rewritten on every call (every word
+  // of the array is written before it is read within a call; nothing needs
+  // clearing). The launches copy their parameters when they are issued, so
+  // the host table is free again when they return.
   PhaseTable tab;
-  tab.two_level = T > kDirectTableMax;
-  tab.entries = tab.two_level ? 256u + (T + 255u) / 256u : T;
   tab.dev = reinterpret_cast<float2*>(static_cast<char*>(base) + kNoAllocScratchMax);
-  k_noalloc_phase_table<<<(tab.entries + 255u) / 256u, 256, 0, s>>>(T, tab.entries, tab.two_level ? 1 : 0, tab.dev);
-  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    tab.entries = phase_table_host(T, g_noalloc_host_table, &tab.two_level);
+    for (uint32_t first = 0; first < tab.entries; first += kNoAllocTableChunk) {
+      const uint32_t count = std::min(kNoAllocTableChunk, tab.entries - first);
+      TableChunk c;
+      std::memcpy(c.v, g_noalloc_host_table + first, size_t(count) * sizeof(float2));
+      k_noalloc_put_table<<<1, 256, 0, s>>>(c, first, count, tab.dev);
+      SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+    }
+  }
   const Scratch sc = carve(base, P, params->k_max);
   const float2* zz = reinterpret_cast<const float2*>(z);
   switch (params->k_max) {
-    case 1: return run<1>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
-    case 2: return run<2>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
-    case 3: return run<3>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
-    default: return run<4>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab, s);
+    case 1: return run<1>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab,
+                            ctx->d_flags, false, s);
+    case 2: return run<2>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab,
+                            ctx->d_flags, false, s);
+    case 3: return run<3>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab,
+                            ctx->d_flags, false, s);
+    default: return run<4>(ctx, zz, n, rows, cols, T, m, h, *params, depth, alpha, active, alpha0, sc, tab,
+                           ctx->d_flags, false, s);
   }
 }
 

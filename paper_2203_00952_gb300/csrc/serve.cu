@@ -14,7 +14,12 @@
 // depend on which other frames share the device.
 //
 // Host-side fault injection for tests: SRT3D_FAULT=alloc makes the next
-// admission fail with SRT3D_ENOMEM as if the allocation had failed.
+// admission fail with SRT3D_ENOMEM as if the allocation had failed;
+// SRT3D_FAULT=gridwait:<frame id> launches that frame's persistent iteration
+// kernel with a grid-barrier target one arrival beyond what its grid delivers
+// and a ~50 us wait limit, so its barrier waits give up (the kernel returns,
+// latching FLAG_DEVICE_TIMEOUT in the frame's own error word) and its poll
+// returns SRT3D_ETIMEDOUT; the other frames are untouched.
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -316,8 +321,11 @@ extern "C" srt3d_status srt3d_submit(srt3d_ctx* ctx, uint64_t frame_id, uint32_t
     if (st != SRT3D_OK) return st;
     srt3d_params prm = f->prm;
     prm.init_mode = SRT3D_INIT_MATCHED;
+    bool inject = false;
+    if (const char* e = std::getenv("SRT3D_FAULT"))
+      if (std::strncmp(e, "gridwait:", 9) == 0) inject = std::strtoull(e + 9, nullptr, 10) == frame_id;
     st = reconstruct_impl(ctx, f->S, f->n, rows, cols, T, m, f->h, prm, f->depth, f->alpha, f->active, f->alpha0,
-                          f->scratch, f->scratch_bytes, s.stream);
+                          f->scratch, f->scratch_bytes, s.stream, f->flags, inject);
     if (st != SRT3D_OK) return st;
     const size_t K = prm.k_max;
     st = grow_pinned(ctx, &s.pin_out, &s.pin_out_bytes, out_bytes(f));
@@ -383,5 +391,7 @@ extern "C" srt3d_status srt3d_poll(srt3d_ctx* ctx, uint64_t frame_id, uint32_t t
   release_frame(ctx, sv, f);
   if (flags & FLAG_OFFSETS) return set_error(ctx, SRT3D_EOFFSETS, "malformed offsets in a chunk");
   if (flags & FLAG_STAMP_RANGE) return set_error(ctx, SRT3D_ERANGE, "a stamp >= T in a chunk");
+  if (flags & FLAG_DEVICE_TIMEOUT)
+    return set_error(ctx, SRT3D_ETIMEDOUT, "a device wait of the frame's reconstruction gave up (partial result)");
   return SRT3D_OK;
 }

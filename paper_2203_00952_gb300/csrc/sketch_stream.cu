@@ -37,31 +37,18 @@ constexpr int kRestart = 8;       // direct table: restart every kRestart harmon
 constexpr int kRestartAbove = 10;  // ... when m exceeds this
 constexpr int kResyncTL = 16;      // two-level table: resync of the rotation
 
-// acc[j-1] += s_j e^{i w_j x} for j = 1..M, s_j = -1 when j mod 4 is 2 or 3
-// (the caller flips those signs once per pixel); acc holds packed (Re, Im)
-// pairs. Direct table: Chebyshev recurrence. Two-level table (T > 8192): its
-// composed e_1 carries ~1.5 ulp, which the recurrence would amplify ~j^2-fold,
-// so there the harmonics come from complex rotation e_j = e_{j-1} e_1 (error
-// growing ~j-fold), resynced from the table every 16 harmonics, and the signs
-// are applied per term.
-template <int M, bool TL>
-__device__ __forceinline__ void add_photon(pf2 (&acc)[M], uint32_t x, const float2* tab, uint32_t T, float invT) {
-  const pf2* ptab = reinterpret_cast<const pf2*>(tab);
-  if (TL) {
-    const float2 e1 = phase(tab, x, true);
-    float2 e = e1;
-    acc[0] = padd(acc[0], pk(e.x, e.y));
-#pragma unroll
-    for (int j = 2; j <= M; ++j) {
-      if ((j - 1) % kResyncTL == 0)
-        e = phase(tab, mulmod(uint32_t(j), x, T, invT), true);
-      else
-        e = cmul(e, e1);
-      acc[j - 1] = (j & 2) ? psub(acc[j - 1], pk(e.x, e.y)) : padd(acc[j - 1], pk(e.x, e.y));
-    }
-    return;
-  }
-  const pf2 e1 = ptab[x];
+// What a sketch kernel does with its sums: overwrite S, add them into S (the
+// online update of Sec. 2), or overwrite with z = S / n (one-shot batches,
+// which then need no separate normalisation launch).
+enum : int { kOverwrite = 0, kAccumulate = 1, kNormalise = 2 };
+
+// acc[j-1] += s_j e_j, j = 1..M, from e_1 on the direct-table path: the
+// Chebyshev recurrence on the signed sequence (see add_photon), restarted
+// from the table at the exact integer phase every kRestart harmonics when M
+// exceeds kRestartAbove.
+template <int M>
+__device__ __forceinline__ void chebyshev_from(pf2 (&acc)[M], const pf2 e1, uint32_t x, const pf2* ptab, uint32_t T,
+                                               float invT) {
   const float c2 = pk_lo(e1) + pk_lo(e1);
   const pf2 pc = pk(c2, c2), nc = pk(-c2, -c2);
   pf2 p = pk(1.f, 0.f);  // a_{j-2}
@@ -86,6 +73,66 @@ __device__ __forceinline__ void add_photon(pf2 (&acc)[M], uint32_t x, const floa
   }
 }
 
+// acc[j-1] += s_j e^{i w_j x} for j = 1..M, s_j = -1 when j mod 4 is 2 or 3
+// (the caller flips those signs once per pixel); acc holds packed (Re, Im)
+// pairs. Direct table: Chebyshev recurrence. Two-level table (T > 8192): its
+// composed e_1 carries ~1.5 ulp, which the recurrence would amplify ~j^2-fold,
+// so there the harmonics come from complex rotation e_j = e_{j-1} e_1 (error
+// growing ~j-fold), resynced from the table every 16 harmonics, and the signs
+// are applied per term.
+template <int M, bool TL>
+__device__ __forceinline__ void add_photon(pf2 (&acc)[M], uint32_t x, const float2* tab, uint32_t T, float invT) {
+  const pf2* ptab = reinterpret_cast<const pf2*>(tab);
+  if (TL) {
+    const float2 e1 = phase(tab, x, true);
+    float2 e = e1;
+    acc[0] = padd(acc[0], pk(e.x, e.y));
+#pragma unroll
+    for (int j = 2; j <= M; ++j) {
+      if ((j - 1) % kResyncTL == 0)
+        e = phase(tab, mulmod(uint32_t(j), x, T, invT), true);
+      else
+        e = cmul(e, e1);
+      acc[j - 1] = (j & 2) ? psub(acc[j - 1], pk(e.x, e.y)) : padd(acc[j - 1], pk(e.x, e.y));
+    }
+    return;
+  }
+  chebyshev_from<M>(acc, ptab[x], x, ptab, T, invT);
+}
+
+// Stamps of each 16-byte word (of 8) whose first-harmonic phasor comes from
+// the special-function unit instead of the table, direct-table path only. At
+// one or two harmonics the table lookups (random indices: ~6 shared-memory
+// wavefronts per warp-wide lookup) keep the L1/shared pipe busier than HBM
+// keeps the loads (81 % L1TEX throughput at m = 1); computing half of the
+// phasors on the SFU, which no other stage uses, shares that load (12 % faster
+// at m = 1). From three harmonics on the extra work of forming harmonics from
+// an SFU phasor costs more than it saves, and every phasor comes from the table.
+template <int M>
+constexpr int sfu_photons() {
+  return M <= 2 ? 4 : 0;
+}
+
+// add_photon (direct table) with e_1 = (cos, sin)(2 pi x' / T) from the SFU:
+// x' = x or x - T, the exactly reduced phase in [-T/2, T/2), so the argument
+// lies in [-pi, pi) where the SFU's sine and cosine are accurate to ~4e-7
+// absolute; harmonic 2 follows the Chebyshev step (error ~2x that of e_1).
+template <int M>
+__device__ __forceinline__ void add_photon_sfu(pf2 (&acc)[M], uint32_t x, uint32_t T, float w1) {
+  if constexpr (M <= 2) {  // (sfu_photons is 0 above two harmonics)
+    const int xr = int(x) - ((2u * x >= T) ? int(T) : 0);
+    float sn, cs;
+    __sincosf(float(xr) * w1, &sn, &cs);
+    const pf2 e1 = pk(cs, sn);
+    acc[0] = padd(acc[0], e1);
+    if constexpr (M == 2) {
+      // a_2 = -e_2 = e_0 - 2 cos(w x) e_1 (signed sequence, s_2 = -1)
+      const pf2 a2 = pfma(pk(-2.f * cs, -2.f * cs), e1, pk(1.f, 0.f));
+      acc[1] = padd(acc[1], a2);
+    }
+  }
+}
+
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -101,47 +148,116 @@ __device__ __forceinline__ void word_photons(pf2 (&acc)[M], const uint4 v, const
   const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
                          v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
   uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
+  constexpr int NS = TL ? 0 : sfu_photons<M>();
+  const float w1 = 6.283185307179586f * invT;
   if (mx < T) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+    for (int i = 0; i < 8; ++i) {
+      if (i >= 8 - NS)
+        add_photon_sfu<M>(acc, x[i], T, w1);
+      else
+        add_photon<M, TL>(acc, x[i], s_tab, T, invT);
+    }
   } else {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      if (x[i] < T)
-        add_photon<M, TL>(acc, x[i], s_tab, T, invT);
-      else
+      if (x[i] >= T)
         bad = true;
+      else if (i >= 8 - NS)
+        add_photon_sfu<M>(acc, x[i], T, w1);
+      else
+        add_photon<M, TL>(acc, x[i], s_tab, T, invT);
     }
   }
 }
 
-// All photons of one pixel for lane gl of its group: the loose stamps one
-// per lane, then whole words. The lane's first word is requested before the
-// loose stamps are processed and each next word before the current one, so
-// one load is always in flight. Returns whether a stamp was >= T.
-template <int M, bool TL>
-__device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const uint4* __restrict__ words,
-                                              const uint16_t* __restrict__ half, uint32_t a, uint32_t b,
-                                              uint32_t nh, uint32_t nl, uint32_t ts, uint32_t wa, uint32_t wb,
+// Positions of one pixel's stamps relative to the aligned base of the stamp
+// array: [a, b). Derived: whole 16-byte words [wa, wb) = [ceil(a/8), floor(b/8)),
+// loose stamps [a, he) and [ts, b) in the partial first and last words (nl of
+// them, nh in the first). Only a and b are kept in registers.
+struct PixelSpan {
+  uint32_t a, b;
+  __device__ __forceinline__ uint32_t wa() const { return (a + 7u) >> 3; }
+  __device__ __forceinline__ uint32_t wb() const { return b >> 3; }
+  __device__ __forceinline__ uint32_t he() const { return min(b, wa() << 3); }
+  __device__ __forceinline__ uint32_t ts() const { return max(he(), wb() << 3); }
+  __device__ __forceinline__ uint32_t nh() const { return he() - a; }
+  __device__ __forceinline__ uint32_t nl() const { return nh() + (b - ts()); }
+  // position of the i-th loose stamp (i < nl)
+  __device__ __forceinline__ uint32_t loose(uint32_t i) const { return i < nh() ? a + i : ts() + (i - nh()); }
+};
+
+// Span of CSR offsets (s, e); malformed offsets (e < s or e > num_stamps)
+// give an empty span and set `bad`.
+__device__ __forceinline__ PixelSpan pixel_span(uint32_t s, uint32_t e, uint32_t shift, uint32_t num_stamps,
+                                                bool& bad) {
+  if (e < s || e > num_stamps) {
+    bad = true;
+    s = e = 0;
+  }
+  return PixelSpan{s + shift, e + shift};
+}
+
+// The loads of one pixel that lane gl issues ahead of its use: its first D
+// whole words (wa + gl + j G) and its first loose stamp (~0u: none).
+template <int D>
+struct PixelLoads {
+  uint4 w[D];
+  uint32_t loose;
+};
+
+template <int D>
+__device__ __forceinline__ void issue_loads(PixelLoads<D>& L, const PixelSpan& r, const uint4* __restrict__ words,
+                                            const uint16_t* __restrict__ half, uint32_t G, uint32_t gl) {
+  const uint32_t wa = r.wa(), wb = r.wb();
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const uint32_t w = wa + gl + uint32_t(j) * G;
+    L.w[j] = make_uint4(0u, 0u, 0u, 0u);
+    if (w < wb) L.w[j] = ld_stream(words + w);
+  }
+  L.loose = 0xffffffffu;
+  if (gl < r.nl()) L.loose = __ldg(half + r.loose(gl));
+}
+
+// All photons of one pixel for lane gl, from loads issued one pixel ahead:
+// the prefetched loose stamp and words, then the lane's further loose stamps
+// (groups narrower than the pixel's loose-stamp count) and whole words (one
+// load ahead). Returns whether a stamp was >= T.
+template <int M, bool TL, int D>
+__device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const PixelLoads<D>& L, const PixelSpan& r,
+                                              const uint4* __restrict__ words, const uint16_t* __restrict__ half,
                                               uint32_t T, float invT, uint32_t G, uint32_t gl, const float2* s_tab) {
   bool bad = false;
-  uint32_t w = wa + gl;
-  uint4 v = make_uint4(0u, 0u, 0u, 0u);
-  if (w < wb) v = ld_stream(words + w);
-  for (uint32_t i = gl; i < nl; i += G) {
-    const uint32_t x = __ldg(half + (i < nh ? a + i : ts + (i - nh)));
+  if (L.loose != 0xffffffffu) {
+    if (L.loose < T)
+      add_photon<M, TL>(acc, L.loose, s_tab, T, invT);
+    else
+      bad = true;
+  }
+  for (uint32_t i = gl + G; i < r.nl(); i += G) {
+    const uint32_t x = __ldg(half + r.loose(i));
     if (x < T)
       add_photon<M, TL>(acc, x, s_tab, T, invT);
     else
       bad = true;
   }
-  while (w < wb) {
-    const uint32_t wn = w + G;
-    uint4 vn = make_uint4(0u, 0u, 0u, 0u);
-    if (wn < wb) vn = ld_stream(words + wn);
-    word_photons<M, TL>(acc, v, s_tab, T, invT, bad);
-    v = vn;
-    w = wn;
+  const uint32_t wa = r.wa(), wb = r.wb();
+#pragma unroll
+  for (int j = 0; j < D; ++j)
+    if (wa + gl + uint32_t(j) * G < wb) word_photons<M, TL>(acc, L.w[j], s_tab, T, invT, bad);
+  uint32_t w = wa + gl + uint32_t(D) * G;
+  if (w < wb) {
+    uint4 v = ld_stream(words + w);
+    for (;;) {
+      const uint32_t wn = w + G;
+      uint4 vn = make_uint4(0u, 0u, 0u, 0u);
+      if (wn < wb) vn = ld_stream(words + wn);
+      word_photons<M, TL>(acc, v, s_tab, T, invT, bad);
+      if (wn >= wb) break;
+      v = vn;
+      w = wn;
+    }
   }
   return bad;
 }
@@ -191,7 +307,7 @@ __device__ __forceinline__ void reduce_scatter(const float (&v)[L], uint32_t gl,
 // accumulated) into S[p][0..m): each lane stores the entries it holds.
 template <int M, int LG>
 __device__ __forceinline__ void store_sums(const pf2 (&acc)[M], uint32_t gl, unsigned gmask, uint32_t m,
-                                           int accumulate, float* __restrict__ Sp) {
+                                           int accumulate, uint32_t count, float* __restrict__ Sp) {
   float v[2 * M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -207,51 +323,88 @@ __device__ __forceinline__ void store_sums(const pf2 (&acc)[M], uint32_t gl, uns
     const uint32_t idx = base + uint32_t(i);
     if (uint32_t(i) < cnt && idx < 2u * m) {
       float x = ((idx >> 1) + 1u) & 2u ? -res[i] : res[i];
-      if (accumulate) x += Sp[idx];
+      if (accumulate == kAccumulate) x += Sp[idx];
+      if (accumulate == kNormalise) x = count ? x / float(count) : 0.f;  // z = S / n as k_finalize rounds it
       Sp[idx] = x;
     }
   }
 }
 
-// One pixel of the stream, processed by a group of G lanes: coalesced 16-byte
-// words from the aligned base, per-lane partial sums, xor-shuffle reduction,
-// store (or accumulate) of S[p][0..m) and n[p].
-// (s, e) = offsets[p], offsets[p + 1], already loaded by the caller.
-template <int M>
-__device__ __forceinline__ void sketch_pixel(const uint4* __restrict__ words, uint32_t shift, uint32_t s,
-                                             uint32_t e, uint32_t num_stamps, uint32_t p, uint32_t T, float invT,
-                                             uint32_t m, uint32_t G, uint32_t gl, unsigned gmask, int accumulate,
-                                             const float2* s_tab, bool tl, float2* __restrict__ S,
-                                             uint32_t* __restrict__ n, uint32_t* __restrict__ flags) {
-  if (e < s || e > num_stamps) {
-    if (gl == 0) atomicOr(flags, FLAG_OFFSETS);
-    s = e = 0;
-  }
-  pf2 acc[M];
-#pragma unroll
-  for (int j = 0; j < M; ++j) acc[j] = 0ull;  // (+0, +0)
-  // positions relative to the aligned base; whole words [wa, wb), loose
-  // stamps [a, he) and [ts, b)
-  const uint32_t a = s + shift, b = e + shift;
-  const uint32_t wa = (a + 7u) >> 3, wb = b >> 3;
-  const uint32_t he = min(b, wa << 3), ts = max(he, wb << 3);
-  const uint32_t nh = he - a, nl = nh + (b - ts);
+// Pixels p0, p0 + step, ... < p1 of the stream, each processed by this
+// group of G lanes: coalesced 16-byte words from the aligned base, per-lane
+// partial sums, xor-shuffle reduce-scatter, store (or accumulate) of
+// S[p][0..m) and n[p]. The loads of the next pixel (its first D words per lane
+// and its first loose stamp) are issued before the current pixel is
+// processed, and the offsets of the pixel after it one pixel earlier still,
+// so 2D words per lane can be in flight and no pixel starts with an idle load
+// latency.
+template <int M, bool TL, int D>
+__device__ __forceinline__ void sketch_pixels(const uint4* __restrict__ words, uint32_t shift,
+                                              const uint32_t* __restrict__ offsets, uint32_t num_stamps, uint32_t p0,
+                                              uint32_t p1, uint32_t step, uint32_t T, float invT, uint32_t m,
+                                              uint32_t G, uint32_t gl, unsigned gmask, int accumulate,
+                                              const float2* s_tab, float2* __restrict__ S, uint32_t* __restrict__ n,
+                                              uint32_t* __restrict__ flags) {
+  if (p0 >= p1) return;
   const uint16_t* half = reinterpret_cast<const uint16_t*>(words);
-  const bool bad = tl ? pixel_photons<M, true>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab)
-                      : pixel_photons<M, false>(acc, words, half, a, b, nh, nl, ts, wa, wb, T, invT, G, gl, s_tab);
-  if (bad) atomicOr(flags, FLAG_STAMP_RANGE);
-  float* Sp = reinterpret_cast<float*>(S + size_t(p) * m);
-  switch (G) {
-    case 4: store_sums<M, 2>(acc, gl, gmask, m, accumulate, Sp); break;
-    case 8: store_sums<M, 3>(acc, gl, gmask, m, accumulate, Sp); break;
-    case 16: store_sums<M, 4>(acc, gl, gmask, m, accumulate, Sp); break;
-    default: store_sums<M, 5>(acc, gl, gmask, m, accumulate, Sp); break;
+  bool bad_off = false;
+  PixelSpan cur = pixel_span(__ldg(offsets + p0), __ldg(offsets + p0 + 1), shift, num_stamps, bad_off);
+  PixelLoads<D> lc;
+  issue_loads<D>(lc, cur, words, half, G, gl);
+  // offsets of the next pixel
+  uint32_t sn = 0, en = 0;
+  if (uint64_t(p0) + step < p1) {
+    sn = __ldg(offsets + p0 + step);
+    en = __ldg(offsets + p0 + step + 1);
   }
-  if (gl == 0) n[p] = (accumulate ? n[p] : 0u) + (e - s);
+  for (uint32_t p = p0; p < p1; p += step) {
+    const bool more = uint64_t(p) + step < p1;
+    PixelSpan nxt{0u, 0u};
+    PixelLoads<D> ln;
+    if (more) {
+      nxt = pixel_span(sn, en, shift, num_stamps, bad_off);
+      issue_loads<D>(ln, nxt, words, half, G, gl);
+      if (uint64_t(p) + 2ull * step < p1) {
+        sn = __ldg(offsets + p + 2 * step);
+        en = __ldg(offsets + p + 2 * step + 1);
+      }
+    }
+    pf2 acc[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) acc[j] = 0ull;  // (+0, +0)
+    if (pixel_photons<M, TL, D>(acc, lc, cur, words, half, T, invT, G, gl, s_tab)) atomicOr(flags, FLAG_STAMP_RANGE);
+    float* Sp = reinterpret_cast<float*>(S + size_t(p) * m);
+    switch (G) {
+      case 4: store_sums<M, 2>(acc, gl, gmask, m, accumulate, cur.b - cur.a, Sp); break;
+      case 8: store_sums<M, 3>(acc, gl, gmask, m, accumulate, cur.b - cur.a, Sp); break;
+      case 16: store_sums<M, 4>(acc, gl, gmask, m, accumulate, cur.b - cur.a, Sp); break;
+      default: store_sums<M, 5>(acc, gl, gmask, m, accumulate, cur.b - cur.a, Sp); break;
+    }
+    if (gl == 0) n[p] = (accumulate == kAccumulate ? n[p] : 0u) + (cur.b - cur.a);
+    if (more) {
+      cur = nxt;
+      lc = ln;
+    }
+  }
+  if (bad_off && gl == 0) atomicOr(flags, FLAG_OFFSETS);
+}
+
+// Words per lane requested one pixel ahead: deeper where the arithmetic per
+// photon is light (few harmonics: bound by the loads in flight), one where
+// the registers hold many partial sums (bound by the FP32 pipe).
+template <int M>
+constexpr int prefetch_depth() {
+  return M <= 2 ? 2 : 1;
+}
+
+// Co-resident CTAs per SM the register allocation is held to.
+template <int M>
+constexpr int sketch_min_blocks() {
+  return M <= 10 ? 4 : (M <= 16 ? 3 : 2);
 }
 
 template <int M>
-__global__ void __launch_bounds__(kBlock, M <= 10 ? 4 : (M <= 16 ? 3 : 2)) k_sketch_stream(
+__global__ void __launch_bounds__(kBlock, sketch_min_blocks<M>()) k_sketch_stream(
     const uint16_t* __restrict__ stamps, const uint32_t* __restrict__ offsets, uint32_t num_stamps,
     uint32_t P, uint32_t T, uint32_t m, int glog2, int accumulate, const float2* __restrict__ table,
     uint32_t tab_entries, int two_level, float2* __restrict__ S, uint32_t* __restrict__ n,
@@ -259,7 +412,6 @@ __global__ void __launch_bounds__(kBlock, M <= 10 ? 4 : (M <= 16 ? 3 : 2)) k_ske
   extern __shared__ float2 s_tab[];
   for (uint32_t i = threadIdx.x; i < tab_entries; i += blockDim.x) s_tab[i] = table[i];
   __syncthreads();
-  const bool tl = two_level != 0;
   const float invT = 1.0f / float(T);
   const uint32_t G = 1u << glog2;
   const uint32_t lane = threadIdx.x & 31u;
@@ -270,30 +422,24 @@ __global__ void __launch_bounds__(kBlock, M <= 10 ? 4 : (M <= 16 ? 3 : 2)) k_ske
   const uintptr_t addr = reinterpret_cast<uintptr_t>(stamps);
   const uint4* words = reinterpret_cast<const uint4*>(addr & ~uintptr_t(15));
   const uint32_t shift = uint32_t(addr & 15u) >> 1;
-  // the next pixel's offsets are requested before the current pixel runs
-  uint32_t sn = 0, en = 0;
-  if (gid < P) {
-    sn = __ldg(offsets + gid);
-    en = __ldg(offsets + gid + 1);
-  }
-  for (uint32_t p = gid; p < P; p += ngroups) {
-    const uint32_t s = sn, e = en;
-    if (uint64_t(p) + ngroups < P) {
-      sn = __ldg(offsets + p + ngroups);
-      en = __ldg(offsets + p + ngroups + 1);
-    }
-    sketch_pixel<M>(words, shift, s, e, num_stamps, p, T, invT, m, G, gl, gmask, accumulate, s_tab, tl, S, n,
-                    flags);
-  }
+  constexpr int D = prefetch_depth<M>();
+  if (two_level)
+    sketch_pixels<M, true, D>(words, shift, offsets, num_stamps, gid, P, ngroups, T, invT, m, G, gl, gmask,
+                              accumulate, s_tab, S, n, flags);
+  else
+    sketch_pixels<M, false, D>(words, shift, offsets, num_stamps, gid, P, ngroups, T, invT, m, G, gl, gmask,
+                               accumulate, s_tab, S, n, flags);
 }
 
 // Batched sketch of several frames in one persistent launch: the work list
 // holds (frame, first pixel, last pixel) items of roughly equal photon
 // counts; a CTA walks items blockIdx.x, blockIdx.x + gridDim.x, ..., reloading
 // the phase table when the frame changes. Lanes per pixel come from the
-// frame's descriptor (autotuned per photon-density class).
+// frame's descriptor (autotuned per photon-density class). Each pixel's sums
+// are stored normalised, z = S / n, so the batch needs no separate
+// normalisation launch.
 template <int M>
-__global__ void __launch_bounds__(kBlock) k_sketch_batch(const BatchFrame* __restrict__ frames,
+__global__ void __launch_bounds__(kBlock, sketch_min_blocks<M>()) k_sketch_batch(const BatchFrame* __restrict__ frames,
                                                          const uint3* __restrict__ items, uint32_t num_items,
                                                          uint32_t* __restrict__ flags) {
   extern __shared__ float2 s_tab[];
@@ -307,7 +453,6 @@ __global__ void __launch_bounds__(kBlock) k_sketch_batch(const BatchFrame* __res
       __syncthreads();
       cur = item.x;
     }
-    const bool tl = f.two_level != 0;
     const float invT = 1.0f / float(f.T);
     const uint32_t G = 1u << f.glog2;
     const uint32_t lane = threadIdx.x & 31u;
@@ -318,9 +463,13 @@ __global__ void __launch_bounds__(kBlock) k_sketch_batch(const BatchFrame* __res
     const uintptr_t addr = reinterpret_cast<uintptr_t>(f.stamps);
     const uint4* words = reinterpret_cast<const uint4*>(addr & ~uintptr_t(15));
     const uint32_t shift = uint32_t(addr & 15u) >> 1;
-    for (uint32_t p = item.y + gid; p < item.z; p += ngroups)
-      sketch_pixel<M>(words, shift, __ldg(f.offsets + p), __ldg(f.offsets + p + 1), f.num_stamps, p, f.T, invT, f.m,
-                      G, gl, gmask, 0, s_tab, tl, f.S, f.n, flags);
+    constexpr int D = prefetch_depth<M>();
+    if (f.two_level)
+      sketch_pixels<M, true, D>(words, shift, f.offsets, f.num_stamps, item.y + gid, item.z, ngroups, f.T, invT, f.m,
+                                G, gl, gmask, kNormalise, s_tab, f.S, f.n, flags);
+    else
+      sketch_pixels<M, false, D>(words, shift, f.offsets, f.num_stamps, item.y + gid, item.z, ngroups, f.T, invT,
+                                 f.m, G, gl, gmask, kNormalise, s_tab, f.S, f.n, flags);
   }
 }
 
@@ -372,17 +521,6 @@ __global__ void k_finalize(const float2* __restrict__ S, const uint32_t* __restr
   const float2 s = S[i];
   const float nf = float(cnt);
   z[i] = cnt ? make_float2(s.x / nf, s.y / nf) : make_float2(0.f, 0.f);
-}
-
-// z = S / n for every frame of a batch (blockIdx.y = frame).
-__global__ void k_finalize_batch(const BatchFrame* __restrict__ frames) {
-  const BatchFrame& f = frames[blockIdx.y];
-  const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= size_t(f.P) * f.m) return;
-  const uint32_t cnt = f.n[i / f.m];
-  const float2 s = f.S[i];
-  const float nf = float(cnt);
-  f.S[i] = cnt ? make_float2(s.x / nf, s.y / nf) : make_float2(0.f, 0.f);
 }
 
 // One warp per pixel at a time, with 8 KB of shared-memory counters per warp
@@ -580,16 +718,6 @@ srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n,
   const uint32_t grid = uint32_t((total + kBlock - 1) / kBlock);
   const ProfMark mk = prof_begin(ctx, KID_FINALIZE, stream);
   k_finalize<<<grid, kBlock, 0, stream>>>(S, n, P, m, z);
-  prof_end(ctx, KID_FINALIZE, mk, stream);
-  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
-  return SRT3D_OK;
-}
-
-srt3d_status launch_finalize_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, uint32_t max_pm,
-                                   cudaStream_t stream) {
-  const dim3 grid((max_pm + kBlock - 1) / kBlock, nframes);
-  const ProfMark mk = prof_begin(ctx, KID_FINALIZE, stream);
-  k_finalize_batch<<<grid, kBlock, 0, stream>>>(d_frames);
   prof_end(ctx, KID_FINALIZE, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;

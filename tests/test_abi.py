@@ -41,11 +41,39 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_params_struct_layout_matches_header():
-    # 5 x 32-bit integers, 6 floats, one 32-bit integer, no padding
-    assert ctypes.sizeof(binding.srt3d_params) == 48
+    # 5 x 32-bit integers, 6 floats, two 32-bit integers, no padding
+    assert ctypes.sizeof(binding.srt3d_params) == 52
     assert binding.srt3d_params.apss_h.offset == 20
     assert binding.srt3d_params.min_sep.offset == 40
     assert binding.srt3d_params.weighting.offset == 44
+    assert binding.srt3d_params.birth_every.offset == 48
+
+
+def test_struct_layouts_against_a_c_compiler(tmp_path):
+    # the header compiled by gcc: sizes and offsets of every ABI struct field
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"srt3d_params": binding.srt3d_params, "srt3d_frame": binding.srt3d_frame,
+               "srt3d_plan_info": binding.srt3d_plan_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
 
 
 def test_frame_struct_layout_matches_header():

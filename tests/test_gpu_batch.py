@@ -43,10 +43,12 @@ def host(bufs):
     return {k: v.cpu().numpy().copy() for k, v in bufs.items()}
 
 
-def test_batch_matches_single_frame_path(ctx):
-    K = 2
-    prm = B.make_params(iters=12, k_max=K, d_max=30.0, min_sep=15.0)
-    specs = uneven_specs(14, 3)
+@pytest.mark.parametrize("K,iters,radius,num", [(2, 12, 1, 14), (1, 7, 2, 6), (3, 5, 1, 5)])
+def test_batch_matches_single_frame_path(ctx, K, iters, radius, num):
+    # all iterations of all frames run in one cooperative launch over the
+    # frames' tiles (odd and even iteration counts, radius 1 and 2, K = 1..3)
+    prm = B.make_params(iters=iters, k_max=K, radius=radius, d_max=30.0, min_sep=15.0)
+    specs = uneven_specs(num, 3 + K)
     frames, keep, outs = [], [], []
     for i, (spec, m) in enumerate(specs):
         fr = synth.make_stream_frame(spec, 500 + i)

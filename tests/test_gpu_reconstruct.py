@@ -33,7 +33,7 @@ def gpu_params(p: Params, init_mode, iters=None):
     return B.make_params(iters=p.iters if iters is None else iters, k_max=p.k_max, radius=p.radius,
                          init_mode=init_mode, regularize=int(p.regularize), apss_h=p.apss_h, d_max=p.d_max,
                          depth_scale=p.depth_scale, prune_alpha=p.prune_alpha, smooth_lambda=p.smooth_lambda,
-                         min_sep=p.min_sep, weighting=p.weighting)
+                         min_sep=p.min_sep, weighting=p.weighting, birth_every=p.birth_every)
 
 
 def sketch_frame(ctx, fr, m):
@@ -227,8 +227,7 @@ def test_iterations_more_surfaces(ctx, K):
     init = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p10)[:3]
     g10 = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p10, init=init)
     r10 = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p10, init=init)
-    compare_state(g10, r10, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, f"10 iterations, K = {K}", spec.T,
-                  outlier_frac=2e-3)
+    compare_state(g10, r10, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, f"10 iterations, K = {K}", spec.T)
 
 
 @pytest.mark.parametrize("K", [1, 2])
@@ -329,6 +328,107 @@ def test_full_size_256x256(ctx):
     # quality against the synthetic truth: most first surfaces found within 3 sigma
     d = np.abs(g30[0][:, 0] - fr.truth.depth[:, 0])
     assert np.mean(g30[2][:, 0] & (d <= 3 * spec.sigma)) > 0.9
+
+
+def _noise_free_inputs(spec, seed, m, n_surf=0):
+    """Sketches without photon noise: z = Psi of the true surfaces (at integer
+    depths, Eq. 4 with the background's exact zero), so that a birth that
+    restores a dropped surface is a clear argmax (no FP32/FP64 near-tie).
+    n_surf > 0: that many smooth layers in every pixel, 250 bins apart."""
+    import numpy.random as npr
+
+    if n_surf:
+        truth = synth.make_multi_surface_frame(spec, n_surf, seed).truth
+        for k in range(1, n_surf):
+            truth.depth[:, k] = np.mod(truth.depth[:, 0] + 250.0 * k, spec.T)
+    else:
+        truth = synth.make_truth(spec, npr.default_rng(seed))
+    t_true = np.nan_to_num(np.round(truth.depth), nan=0.0)
+    act_true = np.isfinite(truth.depth)
+    h32 = synth.impulse_response(spec.T, spec.sigma).astype(np.float32)
+    hh = oracle.h_hat(h32.astype(np.float64), m)
+    z_np = oracle.model_cf(t_true, truth.alpha, act_true, hh, spec.T)
+    z32 = np.stack([z_np.real, z_np.imag], -1).astype(np.float32)
+    z_np = z32[..., 0].astype(np.float64) + 1j * z32[..., 1].astype(np.float64)
+    n_np = np.full(spec.num_pixels, 1000, np.int64)
+    z = torch.from_numpy(z32).cuda()
+    n = torch.from_numpy(n_np.astype(np.int32)).cuda()
+    return truth, z, n, z_np, n_np, h32, hh
+
+
+@pytest.mark.parametrize("K,regularize", [(1, True), (2, True), (3, True), (2, False)])
+def test_birth_moves_against_oracle(ctx, K, regularize):
+    # RT3D's birth move (every 3 iterations, not after the last) from an init
+    # whose later surfaces were dropped, on noise-free sketches with as many
+    # surfaces in a pixel as slots (K = 3: three smooth layers everywhere), so
+    # that every birth restores a true surface: the GPU's births and iterations
+    # against the oracle's point by point at the end-to-end tolerances, no
+    # out-of-tolerance point allowed
+    spec = synth.FrameSpec(rows=24, cols=28, T=2048, sigma=4.0, mean_photons=800.0, sbr=2.0, two_surface_frac=0.5,
+                           sep_lo=150.0, sep_hi=400.0)
+    m = 16
+    truth, z, n, z_np, n_np, h32, hh = _noise_free_inputs(spec, 61 + K, m, n_surf=3 if K == 3 else 0)
+    p = oracle_params(iters=10, k_max=K, d_max=24.0, min_sep=12.0, birth_every=3, regularize=regularize)
+    t0, a0, act0, _ = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p)
+    act0[:, 1:] = False
+    a0[:, 1:] = 0.0
+    if K == 1:  # a single slot: drop every tenth pixel's point instead
+        act0[::10, 0] = False
+        a0[::10, 0] = 0.0
+    init = (t0, a0, act0)
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=init)
+    r = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p, init=init)
+    compare_state(g, r, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, f"births, K = {K}", spec.T)
+    born = g[2] & ~act0
+    want = {1: act0[::10, 0].size, 2: (truth.nsurf == 2).sum(), 3: 2 * spec.num_pixels}[K]
+    assert born.sum() >= 0.5 * want
+
+
+def test_birth_moves_on_a_noisy_frame(ctx):
+    # Poisson photons: a birth whose matched-filter argmax is a near-tie may
+    # land a bin apart in FP32 and FP64 (a discrete decision that the two
+    # precisions may take differently), so here the two sides are compared by
+    # what they recover
+    spec = synth.FrameSpec(rows=24, cols=28, T=2048, sigma=4.0, mean_photons=800.0, sbr=2.0, two_surface_frac=0.5,
+                           sep_lo=150.0, sep_hi=400.0)
+    m, K = 16, 2
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, 63, m)
+    p = oracle_params(iters=10, k_max=K, d_max=24.0, min_sep=12.0, birth_every=3)
+    t0, a0, act0, _ = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p)
+    act0[:, 1] = False
+    a0[:, 1] = 0.0
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=(t0, a0, act0))
+    r = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p, init=(t0, a0, act0))
+    has2 = fr.truth.nsurf == 2
+    truth = np.nan_to_num(fr.truth.depth, nan=-1e9)
+
+    def found(st):
+        d = np.abs(st[0][:, :, None] - truth[:, None, :])
+        d = np.minimum(d, spec.T - d)
+        return (np.where(st[2][:, :, None], d, np.inf)[:, :, 1].min(axis=1) <= 3 * spec.sigma)[has2].mean()
+
+    fg, fo = found(g), found(r)
+    assert fo > 0.8 and abs(fg - fo) <= 0.02
+    assert abs(int(g[2].sum()) - int(r[2].sum())) <= max(2, int(0.01 * g[2].size))
+
+
+def test_full_size_256x256_thirty_iterations_from_oracle_init(ctx):
+    # The benchmark's workload end to end from a shared start: the oracle's
+    # matched-filter init, then 30 iterations on each side (the launch shape
+    # the benchmark times: one cooperative launch for all iterations),
+    # compared point by point at the end-to-end tolerances (0.05 bin, 1e-3
+    # relative n * alpha) with activity flips and out-of-tolerance points each
+    # within the 0.1 % budget of discrete decisions taken differently in FP32
+    # and FP64.
+    spec = synth.frame_256x256()
+    m = 10
+    fr, z, n, z_np, n_np, h32, hh = frame_inputs(ctx, spec, synth.SEED_256x256, m)
+    p = oracle_params(iters=30, k_max=2, d_max=6 * spec.sigma, min_sep=3 * spec.sigma)
+    init = oracle.init_matched_filter(z_np, n_np, hh, spec.T, p)[:3]
+    g = gpu_reconstruct(ctx, z, n, spec.rows, spec.cols, spec.T, m, h32, p, init=init)
+    r = oracle.reconstruct(z_np, n_np, spec.rows, spec.cols, spec.T, hh, p, init=init)
+    compare_state(g, r, n_np, DEPTH_TOL, INTENSITY_RTOL, FLIP_FRAC, "256x256, 30 iterations", spec.T,
+                  outlier_frac=FLIP_FRAC)
 
 
 def test_edge_cases(ctx):

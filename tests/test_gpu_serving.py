@@ -223,3 +223,39 @@ def test_serving_matches_direct_entry_points(sctx):
     assert np.array_equal(a[0], d.cpu().numpy())
     assert np.array_equal(a[1], al.cpu().numpy())
     assert np.array_equal(a[2], act.cpu().numpy())
+
+
+def test_device_timeout_is_reported_by_that_frames_poll(sctx):
+    # Host-side injection: the frame named by SRT3D_FAULT=gridwait:<id> runs its
+    # one-launch iteration kernel with a grid-barrier target its grid never
+    # reaches and a short wait limit. Every CTA gives up at the first barrier
+    # and returns (no fault, no hang); the frame's own error word carries the
+    # timeout to its poll. The other frames of the mix are unaffected.
+    fs = frames(3)
+    alone = []
+    for i, (fr, m, prm) in enumerate(fs):
+        submit_all(sctx, 600 + i, fr, m, prm, [(fr.stamps, fr.offsets)])
+        alone.append(poll(sctx, 600 + i, fr, prm))
+    os.environ["SRT3D_FAULT"] = "gridwait:701"
+    try:
+        for i, (fr, m, prm) in enumerate(fs):
+            submit_all(sctx, 700 + i, fr, m, prm, [(fr.stamps, fr.offsets)])
+    finally:
+        del os.environ["SRT3D_FAULT"]
+    for i, (fr, m, prm) in enumerate(fs):
+        o = outputs(fr, prm)
+        st = B.srt3d_poll(sctx, 700 + i, 20_000_000, *o, check=False)
+        if i == 1:
+            assert st == B.SRT3D_ETIMEDOUT
+        else:
+            assert st == B.SRT3D_OK
+            for x, y in zip(alone[i], o):
+                assert np.array_equal(x, y)
+    # the released frame is gone, the context keeps working, nothing leaked
+    # into the context's own error word
+    assert B.srt3d_poll(sctx, 701, 0, *outputs(*fs[1][::2]), check=False) == B.SRT3D_ENOTFOUND
+    fr, m, prm = fs[1]
+    submit_all(sctx, 702, fr, m, prm, [(fr.stamps, fr.offsets)])
+    for x, y in zip(alone[1], poll(sctx, 702, fr, prm)):
+        assert np.array_equal(x, y)
+    assert B.srt3d_sync(sctx, check=False) == B.SRT3D_OK

@@ -63,6 +63,21 @@ def test_sketch_every_phase_single_photon(ctx, T, m, bound):
     assert np.max(np.abs(to_complex(S) - S_ref)) <= bound
 
 
+@pytest.mark.parametrize("T,m", [(4096, 1), (4613, 2), (1024, 3), (4096, 4), (8192, 4)])
+def test_sketch_every_phase_in_whole_words(ctx, T, m):
+    """Pixels of 8 equal stamps x in one aligned 16-byte word, every x in
+    [0, T): the whole-word path, where at few harmonics part of each word's
+    phasors come from the SFU instead of the table. S[x] / 8 is the single
+    term e^{i 2 pi l x / T} of Eq. 3 up to the per-term rounding."""
+    stamps = np.repeat(np.arange(T, dtype=np.uint16), 8)
+    offsets = (8 * np.arange(T + 1)).astype(np.uint32)
+    S, n = gpu_sketch_stream(ctx, stamps, offsets, T, m)
+    B.srt3d_sync(ctx)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, T, m)
+    assert np.array_equal(counts(n), n_ref)
+    assert np.max(np.abs(to_complex(S) - S_ref)) / 8 <= 2e-6
+
+
 def test_sketch_unaligned_stream_base(ctx):
     rng = np.random.default_rng(5)
     T, m = 4096, 10
