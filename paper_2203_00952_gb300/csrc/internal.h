@@ -155,6 +155,9 @@ srt3d_status launch_finalize(srt3d_ctx* ctx, const float2* S, const uint32_t* n,
                              uint32_t m, float2* z, cudaStream_t stream);
 int sketch_round_m(uint32_t m);
 int sketch_default_glog2(double mean_photons_per_pixel);
+// Lanes per pixel (log2) the stream sketch takes for num_stamps photons over
+// P pixels: the context's tuned value for that density class, else the default.
+int sketch_glog2(srt3d_ctx* ctx, uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m);
 srt3d_status launch_sketch_stream_g(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                     uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int accumulate,
                                     float2* S, uint32_t* n, cudaStream_t stream, uint32_t* flags, int glog2);

@@ -677,10 +677,26 @@ struct TileSmem {
   alignas(8) float tm[RH * RW][K];  // depth, or kMaskedDepth for an inactive point
   uint8_t act[RH * RW][K];
   float2 hh[kMaxM];
+  // K = 2: the second points (active in ~13 % of the pixels of a typical
+  // frame) are processed from compact lists instead of as a masked second
+  // pass of every thread: positions whose second normal is needed, own
+  // pixels whose second point is projected, and the projections' results
+  int n_list, p_list;
+  uint16_t nlist[NH * NW];
+  uint16_t plist[kTW * kTH];
+  float2 pres[kTW * kTH];
   __device__ float2* nx() { return reinterpret_cast<float2*>(&n[0][0]); }
   __device__ float2* ny() { return nx() + NH * NW; }
   __device__ float2* nz() { return ny() + NH * NW; }
 };
+
+// Empties the second-point lists of the normals and projection stages (one
+// thread, before a barrier that precedes stage 2).
+template <int K, int R>
+__device__ __forceinline__ void reset_lists(TileSmem<K, R>& sm) {
+  sm.n_list = 0;
+  sm.p_list = 0;
+}
 
 // Region index of the j-th halo pixel of a tile th rows high (top band, side
 // columns, bottom band).
@@ -782,16 +798,27 @@ __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, in
     float2* s_nx = sm.nx();
     float2* s_ny = sm.ny();
     float2* s_nz = sm.nz();
+    // first points by every thread, second points from a compact list
+    // (sm.n_list was zeroed before the barrier that precedes this stage)
     for (int i = tid; i < NH * NW; i += NT) {
       const int lr = i / NW + R, lc = i % NW + R;
       const int q0 = lr * RW + lc;
-      float4 nv[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-        nv[k] = sm.act[q0][k] ? normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[q0][k]) : make_float4(0.f, 0.f, 1.f, 0.f);
-      s_nx[i] = make_float2(nv[0].x, nv[1].x);
-      s_ny[i] = make_float2(nv[0].y, nv[1].y);
-      s_nz[i] = make_float2(nv[0].z, nv[1].z);
+      const float4 nv = sm.act[q0][0] ? normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[q0][0])
+                                      : make_float4(0.f, 0.f, 1.f, 0.f);
+      s_nx[i] = make_float2(nv.x, 0.f);
+      s_ny[i] = make_float2(nv.y, 0.f);
+      s_nz[i] = make_float2(nv.z, 1.f);
+      if (sm.act[q0][1]) sm.nlist[atomicAdd(&sm.n_list, 1)] = uint16_t(i);
+    }
+    __syncthreads();
+    const int cnt = sm.n_list;
+    for (int j = tid; j < cnt; j += NT) {
+      const int i = sm.nlist[j];
+      const int lr = i / NW + R, lc = i % NW + R;
+      const float4 nv = normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[lr * RW + lc][1]);
+      s_nx[i].y = nv.x;
+      s_ny[i].y = nv.y;
+      s_nz[i].y = nv.z;
     }
   } else {
     for (int i = tid; i < NH * NW; i += NT) {
@@ -841,32 +868,58 @@ __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, in
 // origin r0, c0, th rows). Returns whether the thread owns an in-array tile
 // pixel; its new state is then in (tout, aout, aact) and written to global
 // memory.
+// Must be called by every thread of the CTA (for K = 2 it passes barriers).
 template <int K, int R>
 __device__ __forceinline__ bool stage3(TileSmem<K, R>& sm, const Stencil& st, int r0, int c0, int th, float* depth,
                                        float* alpha, uint8_t* active, float* alpha0, float (&tout)[K],
                                        float (&aout)[K], bool (&aact)[K], bool store = true) {
   constexpr int H = TileSmem<K, R>::H, RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
   const int tid = threadIdx.x;
-  if (tid >= kTW * th) return false;
   const int ty = tid / kTW, tx = tid % kTW;
   const int rr = r0 + ty, cc = c0 + tx;
-  if (rr >= int(st.rows) || cc >= int(st.cols)) return false;
+  const bool own = tid < kTW * th && rr < int(st.rows) && cc < int(st.cols);
   const int lr = ty + H, lc = tx + H;
   const int q0 = lr * RW + lc;
   if constexpr (K == 2) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const float tq = sm.t[q0][k];
-      tout[k] = tq;
-      aout[k] = 0.f;
-      aact[k] = false;
-      if (!sm.act[q0][k]) continue;
+    // first points by their owners, second points from a compact list
+    // (sm.p_list was zeroed before an earlier barrier of this iteration)
+    if (own) {
+      const float tq = sm.t[q0][0];
+      tout[0] = tq;
+      aout[0] = 0.f;
+      aact[0] = false;
+      if (sm.act[q0][0]) {
+        float an;
+        tout[0] = project_pair<R>(st, sm.tm, sm.a, sm.nx(), sm.ny(), sm.nz(), RW, NW, lr, lc, tq, sm.a[q0][0],
+                                  &an);
+        aact[0] = an >= st.prune_alpha;
+        aout[0] = aact[0] ? an : 0.f;
+      }
+      if (sm.act[q0][1]) sm.plist[atomicAdd(&sm.p_list, 1)] = uint16_t(tid);
+    }
+    __syncthreads();
+    const int cnt = sm.p_list;
+    for (int j = tid; j < cnt; j += blockDim.x) {
+      const int o = sm.plist[j];
+      const int olr = o / kTW + H, olc = o % kTW + H, oq = olr * RW + olc;
       float an;
-      tout[k] = project_pair<R>(st, sm.tm, sm.a, sm.nx(), sm.ny(), sm.nz(), RW, NW, lr, lc, tq, sm.a[q0][k], &an);
-      aact[k] = an >= st.prune_alpha;
-      aout[k] = aact[k] ? an : 0.f;
+      const float tn = project_pair<R>(st, sm.tm, sm.a, sm.nx(), sm.ny(), sm.nz(), RW, NW, olr, olc, sm.t[oq][1],
+                                       sm.a[oq][1], &an);
+      sm.pres[o] = make_float2(tn, an);
+    }
+    __syncthreads();
+    if (!own) return false;
+    tout[1] = sm.t[q0][1];
+    aout[1] = 0.f;
+    aact[1] = false;
+    if (sm.act[q0][1]) {
+      const float2 res = sm.pres[tid];
+      tout[1] = res.x;
+      aact[1] = res.y >= st.prune_alpha;
+      aout[1] = aact[1] ? res.y : 0.f;
     }
   } else {
+    if (!own) return false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const float tq = sm.t[q0][k];
@@ -951,6 +1004,7 @@ __device__ __forceinline__ void iter_tile(const Stencil st, uint32_t tile_x, uin
   for (int i = tid; i < RH * RW; i += NT)
     stage1_pixel<K, R>(sm, st, i, r0, c0, z, n, T, m, eta_t, eta_a, depth_in, alpha_in, active_in, nullptr,
                        nullptr);
+  if (tid == 0) reset_lists(sm);
   __syncthreads();
   // 2) normals on the tile plus an R halo
   stage2<K, R, NT>(sm, st, kTH);
@@ -1076,8 +1130,11 @@ struct XBuf {
 // published iteration it + 1, which each does only after reading its halo of
 // iteration it from that buffer. The final state goes to the caller's
 // buffers during the last iteration.
-template <int K, int R>
-__global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_persistent(
+// MINB: co-resident CTAs per SM the registers are held to. At radius 1 the
+// kernel exists for 3 (more tiles fit at once) and for 2 (more registers, no
+// spills: used when the frame's tiles fit two per SM).
+template <int K, int R, int MINB>
+__global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
     float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags,
@@ -1157,6 +1214,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_p
       }
       put_state<K, R>(sm, i, ht, ha, hact);
     }
+    if (tid == 0) reset_lists(sm);
     __syncthreads();
     // 3) normals, 4) projection, smoothing and pruning
     stage2<K, R, NT>(sm, st, th);
@@ -1284,6 +1342,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_b
         }
         put_state<K, R>(sm, i, ht, ha, hact);
       }
+      if (tid == 0) reset_lists(sm);
       __syncthreads();
       stage2<K, R, NT>(sm, st, th);
       __syncthreads();
@@ -1347,7 +1406,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
     return SRT3D_EAGAIN;
   } else {
   const size_t zsmem = size_t(kTW) * kTH * (size_t(m) * sizeof(float2) + sizeof(uint32_t));
-  auto fn = k_iter_persistent<K, R>;
+  auto fn = k_iter_persistent<K, R, R == 1 ? 3 : 1>;
   cudaFuncAttributes fa;
   SRT3D_CUDA_TRY(ctx, cudaFuncGetAttributes(&fa, fn));
   if (fa.sharedSizeBytes + zsmem > ctx->smem_optin) return SRT3D_EAGAIN;
@@ -1359,6 +1418,16 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   if (th == 0) return SRT3D_EAGAIN;
   const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
   const uint32_t ntiles = tiles_x * ((st.rows + th - 1) / th);
+  if constexpr (R == 1) {
+    // tiles that fit two per SM: the variant with more registers per thread
+    if (ntiles <= 2u * uint32_t(ctx->num_sms)) {
+      auto fn2 = k_iter_persistent<K, R, 2>;
+      SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
+      int bps2 = 0;
+      SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, fn2, persist_threads<R>(), zsmem));
+      if (bps2 >= 2) fn = fn2;
+    }
+  }
   if (ntiles * kTileFlagStride > kMaxTileFlags) return SRT3D_EAGAIN;
   // exchange buffers: the scratch block's spare region and its alternate state
   const size_t pk = size_t(st.rows) * st.cols * K;

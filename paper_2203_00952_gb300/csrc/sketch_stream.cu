@@ -651,6 +651,19 @@ int sketch_default_glog2(double mean) {
   return mean >= 192.0 ? 5 : mean >= 96.0 ? 4 : mean >= 32.0 ? 3 : 2;
 }
 
+int sketch_glog2(srt3d_ctx* ctx, uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m) {
+  // lanes per pixel: the autotuned value for this density class if there is
+  // one, else a whole warp for dense pixels and narrower groups for sparse ones
+  const double mean = P ? double(num_stamps) / double(P) : 0.0;
+  int glog2 = sketch_default_glog2(mean);
+  const int M = sketch_round_m(m);
+  std::lock_guard<std::mutex> lock(ctx->mu);
+  const int bucket = mean < 1.0 ? 0 : int(std::log2(mean));
+  auto it = ctx->tuned.find((uint64_t(M) << 40) | (uint64_t(T > kDirectTableMax) << 32) | uint64_t(bucket));
+  if (it != ctx->tuned.end()) glog2 = it->second;
+  return glog2;
+}
+
 srt3d_status launch_sketch_stream_g(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
                                     uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int accumulate,
                                     float2* S, uint32_t* n, cudaStream_t stream, uint32_t* flags, int glog2) {
@@ -660,16 +673,7 @@ srt3d_status launch_sketch_stream_g(srt3d_ctx* ctx, const uint16_t* stamps, cons
   const int M = sketch_round_m(m);
   SketchFn fn = sketch_fn(M);
   if (!fn) return set_error(ctx, SRT3D_EINVAL, "unsupported m");
-  if (glog2 < 0) {
-    // lanes per pixel: the autotuned value for this density class if there is
-    // one, else a whole warp for dense pixels and narrower groups for sparse ones
-    const double mean = P ? double(num_stamps) / double(P) : 0.0;
-    glog2 = sketch_default_glog2(mean);
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    const int bucket = mean < 1.0 ? 0 : int(std::log2(mean));
-    auto it = ctx->tuned.find((uint64_t(M) << 40) | (uint64_t(tab.two_level) << 32) | uint64_t(bucket));
-    if (it != ctx->tuned.end()) glog2 = it->second;
-  }
+  if (glog2 < 0) glog2 = sketch_glog2(ctx, num_stamps, P, T, m);
   const size_t smem = size_t(tab.entries) * sizeof(float2);
   if (smem > 48 * 1024)
     SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
