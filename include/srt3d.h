@@ -350,7 +350,8 @@ srt3d_status srt3d_selftest_wait_timeout(srt3d_ctx* ctx, uint64_t wait_cycles, v
  *   sketch_m, init_m     harmonic count the sketch / matched-filter kernels are
  *                        instantiated for (the smallest instantiation >= m)
  *   sketch_lanes         lanes per pixel of the stream sketch at the given mean
- *                        photons per pixel (4, 8, 16 or 32)
+ *                        photons per pixel (4, 8 or 16; a batch's tuner may
+ *                        also choose 32 for a density class)
  *   init_grid_spacing    D of the matched filter's branch and bound: the largest
  *                        power of two <= 64 with w_m^2 D^2 / 8 <= 0.08, w_m =
  *                        2 pi m / T (bounds how far the matched-filter score

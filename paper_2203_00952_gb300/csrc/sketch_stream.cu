@@ -36,6 +36,7 @@ constexpr int kBlock = 256;
 constexpr int kRestart = 8;       // direct table: restart every kRestart harmonics ...
 constexpr int kRestartAbove = 10;  // ... when m exceeds this
 constexpr int kResyncTL = 16;      // two-level table: resync of the rotation
+constexpr int kOrTestMaxM = 4;     // whole-word range test by OR up to this m (then the maximum)
 
 // What a sketch kernel does with its sums: overwrite S, add them into S (the
 // online update of Sec. 2), or overwrite with z = S / n (one-shot batches,
@@ -113,21 +114,26 @@ constexpr int sfu_photons() {
   return M <= 2 ? 4 : 0;
 }
 
-// add_photon (direct table) with e_1 = (cos, sin)(2 pi x' / T) from the SFU:
-// x' = x or x - T, the exactly reduced phase in [-T/2, T/2), so the argument
-// lies in [-pi, pi) where the SFU's sine and cosine are accurate to ~4e-7
-// absolute; harmonic 2 follows the Chebyshev step (error ~2x that of e_1).
+// add_photon (direct table) with e_1 from the special-function unit. The
+// stamp's 16 bits are placed in the mantissa of 2^23 (one byte permute) and
+// 2^23 subtracted, giving x exactly as a float; the phase in revolutions
+// r = x / T - 1/2 lies in [-1/2, 1/2) (exact when T is a power of two), so the
+// SFU sees the argument 2 pi r in [-pi, pi), where its sine and cosine are
+// accurate to ~4e-7 absolute, and e^{i w x} = -e^{i 2 pi r}: the sums take
+// the negated phasor. Harmonic 2 follows the Chebyshev step (error ~2x that
+// of e_1). `sel` picks the stamp's half of the word: 0x5410 low, 0x5432 high.
 template <int M>
-__device__ __forceinline__ void add_photon_sfu(pf2 (&acc)[M], uint32_t x, uint32_t T, float w1) {
+__device__ __forceinline__ void add_photon_sfu(pf2 (&acc)[M], uint32_t word, uint32_t sel, float invT) {
   if constexpr (M <= 2) {  // (sfu_photons is 0 above two harmonics)
-    const int xr = int(x) - ((2u * x >= T) ? int(T) : 0);
+    const float xf = __uint_as_float(__byte_perm(word, 0x4b00u, sel)) - 8388608.0f;
+    const float r = fmaf(xf, invT, -0.5f);
     float sn, cs;
-    __sincosf(float(xr) * w1, &sn, &cs);
-    const pf2 e1 = pk(cs, sn);
-    acc[0] = padd(acc[0], e1);
+    __sincosf(6.283185307179586f * r, &sn, &cs);
+    const pf2 e = pk(cs, sn);  // = -e_1
+    acc[0] = psub(acc[0], e);
     if constexpr (M == 2) {
-      // a_2 = -e_2 = e_0 - 2 cos(w x) e_1 (signed sequence, s_2 = -1)
-      const pf2 a2 = pfma(pk(-2.f * cs, -2.f * cs), e1, pk(1.f, 0.f));
+      // a_2 = -e_2 = e_0 - 2 cos(w x) e_1 = 1 - 2 cs e (signed sequence, s_2 = -1)
+      const pf2 a2 = pfma(pk(-2.f * cs, -2.f * cs), e, pk(1.f, 0.f));
       acc[1] = padd(acc[1], a2);
     }
   }
@@ -141,20 +147,32 @@ __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   return v;
 }
 
-// The 8 stamps of one 16-byte word.
+// The 8 stamps of one 16-byte word. hm has the bits at and above log2 of the
+// largest power of two <= T set in both halves: a word whose OR has none of
+// them holds only stamps < T (one test per word; for T not a power of two the
+// word falls back to the exact maximum, then to per-stamp checks).
 template <int M, bool TL>
 __device__ __forceinline__ void word_photons(pf2 (&acc)[M], const uint4 v, const float2* s_tab, uint32_t T,
-                                             float invT, bool& bad) {
+                                             float invT, uint32_t hm, bool& bad) {
+  const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
   const uint32_t x[8] = {v.x & 0xffffu, v.x >> 16, v.y & 0xffffu, v.y >> 16,
                          v.z & 0xffffu, v.z >> 16, v.w & 0xffffu, v.w >> 16};
-  uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
   constexpr int NS = TL ? 0 : sfu_photons<M>();
-  const float w1 = 6.283185307179586f * invT;
-  if (mx < T) {
+  bool ok;
+  if constexpr (M <= kOrTestMaxM) {
+    ok = ((v.x | v.y | v.z | v.w) & hm) == 0u;
+    if (!ok) {
+      const uint32_t mx = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7])));
+      ok = mx < T;
+    }
+  } else {
+    ok = max(max(max(x[0], x[1]), max(x[2], x[3])), max(max(x[4], x[5]), max(x[6], x[7]))) < T;
+  }
+  if (ok) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if (i >= 8 - NS)
-        add_photon_sfu<M>(acc, x[i], T, w1);
+        add_photon_sfu<M>(acc, wv[i >> 1], (i & 1) ? 0x5432u : 0x5410u, invT);
       else
         add_photon<M, TL>(acc, x[i], s_tab, T, invT);
     }
@@ -164,7 +182,7 @@ __device__ __forceinline__ void word_photons(pf2 (&acc)[M], const uint4 v, const
       if (x[i] >= T)
         bad = true;
       else if (i >= 8 - NS)
-        add_photon_sfu<M>(acc, x[i], T, w1);
+        add_photon_sfu<M>(acc, wv[i >> 1], (i & 1) ? 0x5432u : 0x5410u, invT);
       else
         add_photon<M, TL>(acc, x[i], s_tab, T, invT);
     }
@@ -227,7 +245,8 @@ __device__ __forceinline__ void issue_loads(PixelLoads<D>& L, const PixelSpan& r
 template <int M, bool TL, int D>
 __device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const PixelLoads<D>& L, const PixelSpan& r,
                                               const uint4* __restrict__ words, const uint16_t* __restrict__ half,
-                                              uint32_t T, float invT, uint32_t G, uint32_t gl, const float2* s_tab) {
+                                              uint32_t T, float invT, uint32_t hm, uint32_t G, uint32_t gl,
+                                              const float2* s_tab) {
   bool bad = false;
   if (L.loose != 0xffffffffu) {
     if (L.loose < T)
@@ -245,7 +264,7 @@ __device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const PixelLoads<D>
   const uint32_t wa = r.wa(), wb = r.wb();
 #pragma unroll
   for (int j = 0; j < D; ++j)
-    if (wa + gl + uint32_t(j) * G < wb) word_photons<M, TL>(acc, L.w[j], s_tab, T, invT, bad);
+    if (wa + gl + uint32_t(j) * G < wb) word_photons<M, TL>(acc, L.w[j], s_tab, T, invT, hm, bad);
   uint32_t w = wa + gl + uint32_t(D) * G;
   if (w < wb) {
     uint4 v = ld_stream(words + w);
@@ -253,7 +272,7 @@ __device__ __forceinline__ bool pixel_photons(pf2 (&acc)[M], const PixelLoads<D>
       const uint32_t wn = w + G;
       uint4 vn = make_uint4(0u, 0u, 0u, 0u);
       if (wn < wb) vn = ld_stream(words + wn);
-      word_photons<M, TL>(acc, v, s_tab, T, invT, bad);
+      word_photons<M, TL>(acc, v, s_tab, T, invT, hm, bad);
       if (wn >= wb) break;
       v = vn;
       w = wn;
@@ -283,6 +302,14 @@ __device__ __forceinline__ void reduce_scatter(const float (&v)[L], uint32_t gl,
   if constexpr (LG == 0) {
 #pragma unroll
     for (int i = 0; i < L; ++i) res[i] = v[i];
+  } else if constexpr (L == 1) {
+    // one entry left: a butterfly gives every lane the total (the same sum
+    // on both sides of each exchange), and the group's first lane keeps it
+    float t = v[0];
+#pragma unroll
+    for (int k = LG - 1; k >= 0; --k) t += __shfl_xor_sync(gmask, t, 1u << k);
+    res[0] = t;
+    if (gl & ((1u << LG) - 1u)) cnt = 0u;
   } else {
     constexpr int half = (L + 1) / 2;
     constexpr uint32_t o = 1u << (LG - 1);
@@ -347,6 +374,8 @@ __device__ __forceinline__ void sketch_pixels(const uint4* __restrict__ words, u
                                               uint32_t* __restrict__ flags) {
   if (p0 >= p1) return;
   const uint16_t* half = reinterpret_cast<const uint16_t*>(words);
+  const uint32_t hm16 = (0xffffu << (31 - __clz(T))) & 0xffffu;  // T >= 2
+  const uint32_t hm = hm16 | (hm16 << 16);
   bool bad_off = false;
   PixelSpan cur = pixel_span(__ldg(offsets + p0), __ldg(offsets + p0 + 1), shift, num_stamps, bad_off);
   PixelLoads<D> lc;
@@ -372,7 +401,7 @@ __device__ __forceinline__ void sketch_pixels(const uint4* __restrict__ words, u
     pf2 acc[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) acc[j] = 0ull;  // (+0, +0)
-    if (pixel_photons<M, TL, D>(acc, lc, cur, words, half, T, invT, G, gl, s_tab)) atomicOr(flags, FLAG_STAMP_RANGE);
+    if (pixel_photons<M, TL, D>(acc, lc, cur, words, half, T, invT, hm, G, gl, s_tab)) atomicOr(flags, FLAG_STAMP_RANGE);
     float* Sp = reinterpret_cast<float*>(S + size_t(p) * m);
     switch (G) {
       case 4: store_sums<M, 2>(acc, gl, gmask, m, accumulate, cur.b - cur.a, Sp); break;
@@ -648,7 +677,10 @@ __global__ void __launch_bounds__(kHistWarps * 32) k_hist_from_stream(const uint
 }  // namespace
 
 int sketch_default_glog2(double mean) {
-  return mean >= 192.0 ? 5 : mean >= 96.0 ? 4 : mean >= 32.0 ? 3 : 2;
+  // dense pixels take half a warp each: two pixels' loads and reductions
+  // overlap in one warp (3 to 7 % faster than a whole warp per pixel at
+  // ~1000 photons per pixel, m = 1 to 10)
+  return mean >= 96.0 ? 4 : mean >= 32.0 ? 3 : 2;
 }
 
 int sketch_glog2(srt3d_ctx* ctx, uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m) {

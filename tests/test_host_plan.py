@@ -27,7 +27,7 @@ def test_frame_of_the_main_workload():
     p = _plan()
     assert p["sketch_m"] == 10 and p["init_m"] == 10
     assert p["init_grid_spacing"] == 32 and p["init_grid_points"] == 128
-    assert p["sketch_lanes"] == 32
+    assert p["sketch_lanes"] == 16
     assert p["tile_height"] == 14 and p["tiles"] == 16 * 19 == 304
 
 
@@ -62,7 +62,7 @@ def test_sketch_lanes_follow_the_photon_density():
     lanes = [_plan(mean=x)["sketch_lanes"] for x in (0.0, 1.0, 10.0, 50.0, 100.0, 200.0, 1000.0, 1e6)]
     assert all(v in (4, 8, 16, 32) for v in lanes)
     assert lanes == sorted(lanes)
-    assert lanes[0] == 4 and lanes[-1] == 32
+    assert lanes[0] == 4 and lanes[-1] == 16
 
 
 def test_tile_plan_fits_the_device_at_once():
