@@ -75,80 +75,89 @@ Scratch carve(void* base, uint32_t P, uint32_t K) {
   return s;
 }
 
-__device__ __forceinline__ void load_table(float2* s_tab, const float2* table, uint32_t entries) {
-  for (uint32_t i = threadIdx.x; i < entries; i += blockDim.x) s_tab[i] = table[i];
-  __syncthreads();
-}
-
-// One block: hhat (one warp per harmonic), H, and the step-size bases
-// eta_t * n_max, eta_alpha * n_max; n_max itself is left to the init kernels,
-// which read every pixel's count anyway.
-constexpr uint32_t kPrepChunk = 4096;
+// One block: hhat, H and the step-size bases eta_t * n_max, eta_alpha *
+// n_max; n_max itself is left to the init kernels, which read every pixel's
+// count anyway. Every warp works: harmonic l takes floor(32 / m) warps, each
+// summing h(tau) e^{i w_l tau} over its own slice of tau (stride 32 x warps
+// per harmonic), with the exact table index (l tau) mod T advanced by integer
+// addition; the slices are added in slice order by lane l - 1 of warp 0. The
+// phase table is read through L1 (no shared-memory copy).
+constexpr int kPrepUnroll = 8;
 __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uint32_t* __restrict__ n, uint32_t P,
                                           uint32_t T, uint32_t m, uint32_t K, const float2* __restrict__ table,
                                           uint32_t entries, int two_level, float2* __restrict__ hh_out,
-                                          float* __restrict__ misc, float2* s_tab,
-                                          unsigned* __restrict__ tile_flags, uint32_t flag_words) {
-  __shared__ float s_h[kPrepChunk];
+                                          float* __restrict__ misc, unsigned* __restrict__ tile_flags,
+                                          uint32_t flag_words) {
+  __shared__ float3 s_part[32];
   for (uint32_t i = threadIdx.x; i < flag_words; i += blockDim.x) tile_flags[i] = 0u;
-  __shared__ float2 s_hh[32];
-  load_table(s_tab, table, entries);
   const bool tl = two_level != 0;
   const float invT = 1.0f / float(T);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  // warp l - 1 computes hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau}, with its
-  // own H = sum h (m <= 32 warps), over chunks of h staged in shared memory
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t wpl = max(nwarps / m, 1u);  // warps per harmonic (m <= 32)
   float hs = 0.f, re = 0.f, im = 0.f;
-  const uint32_t l = warp + 1u;
-  for (uint32_t base = 0; base < T; base += kPrepChunk) {
-    const uint32_t len = min(kPrepChunk, T - base);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_h[i] = h[base + i];
-    __syncthreads();
-    if (warp < m) {
-      for (uint32_t i = lane; i < len; i += 32u) {
-        const float2 e = phase(s_tab, mulmod(l, base + i, T, invT), tl);
-        const float hv = s_h[i];
-        hs += hv;
-        re = fmaf(hv, e.x, re);
-        im = fmaf(hv, e.y, im);
+  if (warp < wpl * m) {
+    const uint32_t l = warp % m + 1u, slice = warp / m, stride = 32u * wpl;
+    uint32_t tau = slice * 32u + lane;
+    uint32_t k = tau < T ? mulmod(l, tau, T, invT) : 0u;
+    const uint32_t dk = mulmod(l, stride % T, T, invT);
+    // kPrepUnroll terms per pass, their loads issued together (the table and
+    // h come from L2 on first touch); terms past T add exact zeros
+    for (; tau < T; tau += kPrepUnroll * stride) {
+      float hv[kPrepUnroll];
+      float2 e[kPrepUnroll];
+#pragma unroll
+      for (int j = 0; j < kPrepUnroll; ++j) {
+        const uint32_t tj = tau + uint32_t(j) * stride;
+        hv[j] = tj < T ? __ldg(h + tj) : 0.f;
+        e[j] = tj < T ? phase(table, k, tl) : make_float2(0.f, 0.f);
+        k += dk;
+        k -= (k >= T) ? T : 0u;
+      }
+#pragma unroll
+      for (int j = 0; j < kPrepUnroll; ++j) {
+        hs += hv[j];
+        re = fmaf(hv[j], e[j].x, re);
+        im = fmaf(hv[j], e[j].y, im);
       }
     }
   }
-  if (warp < m) {
-    for (int off = 16; off; off >>= 1) {
-      hs += __shfl_xor_sync(0xffffffffu, hs, off);
-      re += __shfl_xor_sync(0xffffffffu, re, off);
-      im += __shfl_xor_sync(0xffffffffu, im, off);
-    }
-    if (lane == 0) {
-      hh_out[l - 1] = make_float2(re / hs, im / hs);
-      s_hh[warp] = make_float2(re / hs, im / hs);
-    }
+  for (int off = 16; off; off >>= 1) {
+    hs += __shfl_xor_sync(0xffffffffu, hs, off);
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
   }
+  if (lane == 0) s_part[warp] = make_float3(hs, re, im);
   __syncthreads();
-  // step-size sums over the harmonics, lane l - 1 of warp 0 taking harmonic l
-  if (warp == 0) {
-    float sw = 0.f, sa = 0.f;
-    if (lane < m) {
-      const float2 v = s_hh[lane];
-      const float a = sqrtf(v.x * v.x + v.y * v.y);
-      const float w = 6.283185307179586f * float(lane + 1u) / float(T);
-      sw = w * w * a * (a + 2.f);
-      sa = a * a;
+  if (warp != 0) return;
+  // lane l - 1 of warp 0: hhat_l from the slices of harmonic l, then the
+  // step-size sums over the harmonics
+  float sw = 0.f, sa = 0.f;
+  if (lane < m) {
+    float H = 0.f, R = 0.f, I = 0.f;
+    for (uint32_t sl = 0; sl < wpl; ++sl) {
+      const float3 v = s_part[sl * m + lane];
+      H += v.x;
+      R += v.y;
+      I += v.z;
     }
-    for (int off = 16; off; off >>= 1) {
-      sw += __shfl_xor_sync(0xffffffffu, sw, off);
-      sa += __shfl_xor_sync(0xffffffffu, sa, off);
-    }
-    if (lane != 0) return;
-    misc[MISC_ETA_T] = 1.f / (2.f * sw);
-    misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
-    misc[MISC_E2] = sa;
-    reinterpret_cast<unsigned*>(misc)[MISC_NMAX] = 0u;  // n_max: atomicMax by the init kernels
-    reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
-    reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // (unused)
+    const float2 v = make_float2(R / H, I / H);
+    hh_out[lane] = v;
+    const float a = sqrtf(v.x * v.x + v.y * v.y);
+    const float w = 6.283185307179586f * float(lane + 1u) / float(T);
+    sw = w * w * a * (a + 2.f);
+    sa = a * a;
   }
+  for (int off = 16; off; off >>= 1) {
+    sw += __shfl_xor_sync(0xffffffffu, sw, off);
+    sa += __shfl_xor_sync(0xffffffffu, sa, off);
+  }
+  if (lane != 0) return;
+  misc[MISC_ETA_T] = 1.f / (2.f * sw);
+  misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
+  misc[MISC_E2] = sa;
+  reinterpret_cast<unsigned*>(misc)[MISC_NMAX] = 0u;  // n_max: atomicMax by the init kernels
+  reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
+  reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // (unused)
 }
 
 __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
@@ -156,16 +165,14 @@ __global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, cons
                                                const float2* __restrict__ table, uint32_t entries, int two_level,
                                                float2* __restrict__ hh_out, float* __restrict__ misc,
                                                unsigned* __restrict__ tile_flags) {
-  extern __shared__ float2 s_tab[];
-  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, s_tab, tile_flags, kMaxTileFlags);
+  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, tile_flags, kMaxTileFlags);
 }
 
 // Batched: one block per frame of the batch (each zeroes its tiles' flags).
 __global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restrict__ frames, uint32_t K,
                                                      unsigned* __restrict__ tile_flags) {
-  extern __shared__ float2 s_tab[];
   const BatchFrame& f = frames[blockIdx.x];
-  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc, s_tab,
+  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc,
             tile_flags + size_t(f.tile0) * kTileFlagStride, f.tiles_x * f.tiles_y * kTileFlagStride);
 }
 
@@ -1463,13 +1470,10 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
                  float* alpha0, const Scratch& sc, const PhaseTable& tab, uint32_t* flags, bool inject_barrier_timeout,
                  cudaStream_t stream) {
   const uint32_t P = rows * cols;
-  const size_t tab_smem = size_t(tab.entries) * sizeof(float2);
   const int tl = tab.two_level ? 1 : 0;
-  // the static h chunk plus the table may exceed the 48 KB default
-  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
-    k_prep<<<1, 1024, tab_smem, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc,
+    k_prep<<<1, 1024, 0, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc,
                                           sc.tile_flags);
     prof_end(ctx, KID_PREP, mk, stream);
   }
@@ -1625,12 +1629,9 @@ template <int K>
 srt3d_status run_batch(srt3d_ctx* ctx, const BatchFrame* d_frames, uint32_t nframes, const InitGroup* groups,
                        uint32_t num_groups, uint32_t total_tiles, uint32_t th, unsigned* tile_flags,
                        uint32_t max_entries, uint32_t max_G, const srt3d_params& prm, cudaStream_t stream) {
-  const size_t tab_smem = size_t(max_entries) * sizeof(float2);
-  SRT3D_CUDA_TRY(ctx,
-                 cudaFuncSetAttribute(k_prep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tab_smem)));
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
-    k_prep_batch<<<nframes, 1024, tab_smem, stream>>>(d_frames, K, tile_flags);
+    k_prep_batch<<<nframes, 1024, 0, stream>>>(d_frames, K, tile_flags);
     prof_end(ctx, KID_PREP, mk, stream);
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
