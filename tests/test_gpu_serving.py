@@ -143,8 +143,10 @@ def test_admission_by_budget(sctx):
     require_gpu()
     fs = frames(3)
     fr0, m0, prm0 = fs[2]  # 32x32
-    # a context whose budget holds about one such frame
-    c2 = B.srt3d_create(0, 180_000)  # one 32x32 frame (~115 kB of device state) fits, two do not
+    # a context whose budget holds one such frame (its device state as the
+    # host plan charges it) and half of a second
+    need = B.srt3d_plan(32, 32, fr0.spec.T, m0, 2, 1, 150.0, 152, 2)["serving_frame_bytes"]
+    c2 = B.srt3d_create(0, int(1.5 * need))
     try:
         h = synth.impulse_response(fr0.spec.T, fr0.spec.sigma).astype(np.float32)
         B.srt3d_submit(c2, 1, 32, 32, fr0.spec.T, m0, h, prm0, fr0.stamps, fr0.offsets, 1)
