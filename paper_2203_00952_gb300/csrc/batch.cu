@@ -233,8 +233,8 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   const size_t frames_bytes = al256(num_frames * sizeof(BatchFrame));
   const size_t scratch_per_frame = 512;  // hhat[32] float2 + misc[8] float
   const uint32_t K = params->k_max;
-  size_t alt_bytes = 0;  // two exchange buffers per frame: depth, alpha (float), active (u8)
-  for (uint32_t i = 0; i < num_frames; ++i) alt_bytes += 6 * al256(size_t(hf[i].P) * K * sizeof(float));
+  size_t alt_bytes = 0;  // two buffers of tagged exchange words per frame, 16 B per point each
+  for (uint32_t i = 0; i < num_frames; ++i) alt_bytes += al256(size_t(hf[i].P) * K * 32);
   // the frames' iteration tiles for a tile height (the tuner tries several)
   const auto layout = [&](uint32_t th) {
     uint32_t tiles = 0;
@@ -256,17 +256,12 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   char* base = static_cast<char*>(e.dmem);
   char* scratch = base + frames_bytes + al256(items_total * sizeof(uint3));
   char* alt = scratch + num_frames * scratch_per_frame;
+  char* const alt0 = alt;  // the tagged words, zeroed before every iteration launch
   for (uint32_t i = 0; i < num_frames; ++i) {
     hf[i].hh = reinterpret_cast<float2*>(scratch + i * scratch_per_frame);
     hf[i].misc = reinterpret_cast<float*>(scratch + i * scratch_per_frame + 256);
-    const size_t pkb = al256(size_t(hf[i].P) * K * sizeof(float));
-    hf[i].depth_alt = reinterpret_cast<float*>(alt);
-    hf[i].alpha_alt = reinterpret_cast<float*>(alt + pkb);
-    hf[i].active_alt = reinterpret_cast<uint8_t*>(alt + 2 * pkb);
-    hf[i].depth_x1 = reinterpret_cast<float*>(alt + 3 * pkb);
-    hf[i].alpha_x1 = reinterpret_cast<float*>(alt + 4 * pkb);
-    hf[i].active_x1 = reinterpret_cast<uint8_t*>(alt + 5 * pkb);
-    alt += 6 * pkb;
+    hf[i].xtag = reinterpret_cast<unsigned long long*>(alt);
+    alt += al256(size_t(hf[i].P) * K * 32);
   }
   unsigned* tile_flags = reinterpret_cast<unsigned*>(alt);
   std::vector<uint3> all_items;
@@ -329,6 +324,7 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
       float ms = 0.f;
       for (int rep = 0; rep < 2 && st == SRT3D_OK; ++rep) {  // the first run warms up
         if (cudaMemsetAsync(tile_flags, 0, flags_bytes, stream) != cudaSuccess ||
+            cudaMemsetAsync(alt0, 0, alt_bytes, stream) != cudaSuccess ||
             cudaEventRecord(ea, stream) != cudaSuccess) {
           st = set_error(ctx, SRT3D_ECUDA, "tuner launch");
           break;
@@ -359,6 +355,8 @@ extern "C" srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* f
   cudaStream_t cs = cache->capture;
   SRT3D_CUDA_TRY(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   st = sketch_all(cs);
+  if (st == SRT3D_OK && cudaMemsetAsync(alt0, 0, alt_bytes, cs) != cudaSuccess)
+    st = set_error(ctx, SRT3D_ECUDA, "exchange words reset");
   if (st == SRT3D_OK)
     st = launch_reconstruct_batch(ctx, d_frames, num_frames, init_groups.data(), uint32_t(init_groups.size()),
                                   tiles, best_th, tile_flags, max_entries, max_G, *params, cs);

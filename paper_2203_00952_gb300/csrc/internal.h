@@ -60,12 +60,9 @@ struct BatchFrame {
   float* alpha0;
   float2* hh;  // per-frame reconstruction scratch: hhat [32], misc [8]
   float* misc;
-  float* depth_alt;  // exchange buffers of the post-gradient state, alternating
-  float* alpha_alt;  // by iteration: (depth_alt, alpha_alt, active_alt) and
-  uint8_t* active_alt;  // (depth_x1, alpha_x1, active_x1)
-  float* depth_x1;
-  float* alpha_x1;
-  uint8_t* active_x1;
+  // tagged exchange words of the post-gradient state, [2][P][K] x 16 B
+  // (alternating by iteration; zeroed before each launch)
+  unsigned long long* xtag;
   uint32_t D;        // matched-filter grid spacing
   uint32_t tile0;    // first iteration tile of this frame in the batch
   uint32_t tiles_x;  // iteration tiles per row (16 pixels wide)

@@ -1358,15 +1358,17 @@ __global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
 // their state in global memory: the frames' own depth/alpha/active buffers,
 // updated in place. Per iteration, phase 1 takes the gradient step of every
 // own tile and publishes its post-gradient state to the frame's exchange
-// buffer of this iteration's parity, raising the tile's progress flag; phase
-// 2, for every own tile, waits for the flags of the tiles its halo touches,
-// loads the post-gradient state of tile + halo, and runs the normals and the
-// projection stages, writing the tile's new state. Phase 1 never waits, and a
-// phase-2 wait is on tiles' phase 1 of the same iteration, which the CTA that
-// is furthest behind can always complete, so the launch cannot deadlock. A
-// tile rewrites the exchange buffer of parity it & 1 in phase 1 of it + 2
-// only after its phase-2 wait of it + 1 saw every tile within reach past
-// phase 1 of it + 1, i.e. past its phase-2 reads of iteration it.
+// words of this iteration's parity, tagged with the iteration (as in
+// k_iter_persistent); phase 2, for every own tile, loads the post-gradient
+// state of tile + halo, each load waiting (bounded) for its words' tag, and
+// runs the normals and the projection stages, writing the tile's new state.
+// Phase 1 never waits, and a phase-2 wait is on tiles' phase 1 of the same
+// iteration, which the CTA that is furthest behind can always complete, so
+// the launch cannot deadlock. A tile rewrites the words of parity it & 1 in
+// phase 1 of it + 2 only after its phase-2 loads of it + 1 returned every
+// tile within reach past phase 1 of it + 1, i.e. past its phase-2 reads of
+// iteration it. The words are zeroed before the launch (tag 0 is no
+// iteration's).
 template <int K, int R>
 __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_batch_persistent(
     Stencil base, const BatchFrame* __restrict__ frames, uint32_t nframes, uint32_t total_tiles, uint32_t th_u,
@@ -1375,7 +1377,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_b
   constexpr int H = S::H, RW = S::RW;
   constexpr int NT = persist_threads<R>();
   const int th = int(th_u), RH = th + 2 * H, npx = kTW * th;
-  const int reach_y = (H + th - 1) / th;
+  (void)tile_flags;  // (the exchange words carry their own tags)
   __shared__ S sm;
   __shared__ int s_abort;
   const int tid = threadIdx.x;
@@ -1410,17 +1412,10 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_b
         const float nmax = float(max(reinterpret_cast<const unsigned*>(f.misc)[MISC_NMAX], 1u));
         grad_pixel<K>(f.S + p * f.m, f.n[p], f.T, f.m, sm.hh, f.misc[MISC_ETA_T] / nmax, f.misc[MISC_ETA_A] / nmax,
                       tq, aq, cq);
-        float* xt = (it & 1u) ? f.depth_x1 : f.depth_alt;
-        float* xa = (it & 1u) ? f.alpha_x1 : f.alpha_alt;
-        uint8_t* xc = (it & 1u) ? f.active_x1 : f.active_alt;
+        unsigned long long* xt = f.xtag + (it & 1u) * (size_t(f.P) * K * 2);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          xt[p * K + k] = tq[k];
-          xa[p * K + k] = aq[k];
-          xc[p * K + k] = cq[k] ? 1 : 0;
-        }
+        for (int k = 0; k < K; ++k) st_tagged2(xt + (p * K + k) * 2, tq[k], cq[k] ? aq[k] : -1.f, it + 1u);
       }
-      tile_publish(tile_flags, tile, it + 1u);
     }
     // phase 2: normals, projection, smoothing and pruning
     for (uint32_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -1439,18 +1434,16 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_b
       const uint32_t t = tile - f.tile0;
       const int tyy = int(t / f.tiles_x), txx = int(t % f.tiles_x);
       const int r0 = tyy * th, c0 = txx * kTW;
-      if (!tile_wait(tile_flags + size_t(f.tile0) * kTileFlagStride, txx, tyy, int(f.tiles_x), int(f.tiles_y),
-                     reach_y, it + 1u, err, &s_abort, kGridWaitCycles))
-        return;  // uniform: every thread read s_abort after the wait's barrier
-      const float* xt = (it & 1u) ? f.depth_x1 : f.depth_alt;
-      const float* xa = (it & 1u) ? f.alpha_x1 : f.alpha_alt;
-      const uint8_t* xc = (it & 1u) ? f.active_x1 : f.active_alt;
+      const unsigned long long* xt = f.xtag + (it & 1u) * (size_t(f.P) * K * 2);
       for (int i = tid; i < RH * RW; i += NT) {
         const int hr = r0 - H + i / RW, hc = c0 - H + i % RW;
         float ht[K], ha[K];
         bool hact[K];
         if (hr >= 0 && hr < int(f.rows) && hc >= 0 && hc < int(f.cols)) {
-          load_state<K>(xt, xa, xc, size_t(hr) * f.cols + size_t(hc), ht, ha, hact);
+          if (!load_state_tagged<K>(xt, size_t(hr) * f.cols + size_t(hc), it + 1u, kGridWaitCycles, ht, ha, hact)) {
+            s_abort = 1;
+            atomicOr(err, FLAG_DEVICE_TIMEOUT);
+          }
         } else {
 #pragma unroll
           for (int k = 0; k < K; ++k) {
@@ -1463,6 +1456,7 @@ __global__ void __launch_bounds__(persist_threads<R>(), R == 1 ? 3 : 1) k_iter_b
       }
       if (tid == 0) reset_lists(sm);
       __syncthreads();
+      if (s_abort) return;  // uniform: read after the barrier
       stage2<K, R, NT>(sm, st, th);
       __syncthreads();
       float tout[K], aout[K];
