@@ -685,6 +685,15 @@ __host__ __device__ constexpr int persist_threads() {
   return R == 1 ? 288 : iter_threads<R>();
 }
 
+// Block of k_iter_persistent<K, R, MINB>: two points per pixel at radius 1
+// with two CTAs per SM take one more warp (the registers allow it), whose
+// threads, with those whose first point is inactive, compute the listed
+// second points' normals in the first points' round.
+template <int K, int R, int MINB>
+__host__ __device__ constexpr int persist_block() {
+  return (K == 2 && R == 1 && MINB == 2) ? 320 : persist_threads<R>();
+}
+
 // Shared memory of one tile: the post-gradient state of the region (tile +
 // 2R halo) with a masked depth copy, and the normals of the tile + R halo
 // (for K = 2 held as component pairs of the two points in the same storage).
@@ -703,7 +712,7 @@ struct TileSmem {
   // frame) are processed from compact lists instead of as a masked second
   // pass of every thread: positions whose second normal is needed, own
   // pixels whose second point is projected, and the projections' results
-  int n_list, p_list;
+  int n_list, p_list, n_take;
   uint16_t nlist[NH * NW];
   uint16_t plist[kTW * kTH];
   float2 pres[kTW * kTH];
@@ -718,6 +727,7 @@ template <int K, int R>
 __device__ __forceinline__ void reset_lists(TileSmem<K, R>& sm) {
   sm.n_list = 0;
   sm.p_list = 0;
+  sm.n_take = 0;
 }
 
 // Region index of the j-th halo pixel of a tile th rows high (top band, side
@@ -811,12 +821,45 @@ __device__ __forceinline__ void stage1_pixel(TileSmem<K, R>& sm, const Stencil& 
 }
 
 // Stage 2: normals of the tile (th rows) plus an R halo, NT threads.
-template <int K, int R, int NT>
+// PRE (K = 2): the second points' positions (sm.nlist) and the tile's own
+// second points (sm.plist) were listed before the stage; every thread takes
+// list items once its first point is done (threads without a first point,
+// or with an inactive one, first), so a short list needs no round of its own.
+template <int K, int R, int NT, bool PRE = false>
 __device__ __forceinline__ void stage2(TileSmem<K, R>& sm, const Stencil& st, int th) {
   constexpr int RW = TileSmem<K, R>::RW, NW = TileSmem<K, R>::NW;
   const int NH = th + 2 * R;
   const int tid = threadIdx.x;
-  if constexpr (K == 2) {
+  if constexpr (K == 2 && PRE) {
+    float2* s_nx = sm.nx();
+    float2* s_ny = sm.ny();
+    float2* s_nz = sm.nz();
+    for (int i = tid; i < NH * NW; i += NT) {
+      const int lr = i / NW + R, lc = i % NW + R;
+      const int q0 = lr * RW + lc;
+      const float4 nv = sm.act[q0][0] ? normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[q0][0])
+                                      : make_float4(0.f, 0.f, 1.f, 0.f);
+      s_nx[i].x = nv.x;
+      s_ny[i].x = nv.y;
+      s_nz[i].x = nv.z;
+      if (!sm.act[q0][1]) {  // (a listed item writes these words otherwise)
+        s_nx[i].y = 0.f;
+        s_ny[i].y = 0.f;
+        s_nz[i].y = 1.f;
+      }
+    }
+    const int cnt = sm.n_list;
+    for (;;) {
+      const int j = atomicAdd(&sm.n_take, 1);
+      if (j >= cnt) break;
+      const int i = sm.nlist[j];
+      const int lr = i / NW + R, lc = i % NW + R;
+      const float4 nv = normal_pair<R>(st, sm.tm, RW, lr, lc, sm.t[lr * RW + lc][1]);
+      s_nx[i].y = nv.x;
+      s_ny[i].y = nv.y;
+      s_nz[i].y = nv.z;
+    }
+  } else if constexpr (K == 2) {
     float2* s_nx = sm.nx();
     float2* s_ny = sm.ny();
     float2* s_nz = sm.nz();
@@ -1232,15 +1275,16 @@ struct XBuf {
 // kernel exists for 3 (more tiles fit at once) and for 2 (more registers, no
 // spills: used when the frame's tiles fit two per SM).
 template <int K, int R, int MINB>
-__global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
+__global__ void __launch_bounds__(persist_block<K, R, MINB>(), MINB) k_iter_persistent(
     Stencil st, const float2* __restrict__ z, const uint32_t* __restrict__ n, uint32_t T, uint32_t m,
     const float2* __restrict__ hh_g, float* __restrict__ misc, float* depth, float* alpha, uint8_t* active,
     float* alpha0, XBuf x0, XBuf x1, uint32_t iters, uint32_t tiles_x, uint32_t th_u, uint32_t* __restrict__ flags,
     unsigned* tile_flags, uint32_t flag_base, uint32_t bar_skew, long long wait_limit,
     unsigned long long* __restrict__ xtag) {
   using S = TileSmem<K, R>;
-  constexpr int H = S::H, RW = S::RW;
-  constexpr int NT = persist_threads<R>();
+  constexpr int H = S::H, RW = S::RW, NW = S::NW;
+  constexpr int NT = persist_block<K, R, MINB>();
+  constexpr bool PRE = K == 2;  // second points listed before the normals stage
   const int th = int(th_u), RH = th + 2 * H, halo = RH * RW - kTW * th, npx = kTW * th;
   __shared__ S sm;
   __shared__ int s_abort;
@@ -1260,7 +1304,10 @@ __global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
     s_nn[q] = rr < int(st.rows) && cc < int(st.cols) ? n[size_t(rr) * st.cols + size_t(cc)] : 0u;
   }
   if (tid < int(m)) sm.hh[tid] = hh_g[tid];
-  if (tid == 0) s_abort = 0;
+  if (tid == 0) {
+    s_abort = 0;
+    reset_lists(sm);
+  }
   __syncthreads();
   const float nmax = float(max(reinterpret_cast<const unsigned*>(misc)[MISC_NMAX], 1u));
   const float eta_t = misc[MISC_ETA_T] / nmax, eta_a = misc[MISC_ETA_A] / nmax;
@@ -1285,6 +1332,12 @@ __global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
     if (mine) {
       grad_to_smem<K, R>(sm, st, (ty + H) * RW + (tx + H), rr, cc, in, t, a, act, z, n, T, m, eta_t, eta_a, s_z,
                          s_nn, tid);
+      if constexpr (PRE) {
+        if (act[K - 1]) {
+          sm.nlist[atomicAdd(&sm.n_list, 1)] = uint16_t((ty + R) * NW + tx + R);
+          sm.plist[atomicAdd(&sm.p_list, 1)] = uint16_t(tid);
+        }
+      }
       if (in) {
         if (xt) {
 #pragma unroll
@@ -1331,12 +1384,17 @@ __global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
         }
       }
       put_state<K, R>(sm, i, ht, ha, hact);
+      if constexpr (PRE) {
+        const int lr = i / RW, lc = i % RW;  // listed when in the normals region
+        if (hact[K - 1] && lr >= R && lr < th + 3 * R && lc >= R && lc < kTW + 3 * R)
+          sm.nlist[atomicAdd(&sm.n_list, 1)] = uint16_t((lr - R) * NW + lc - R);
+      }
     }
-    if (tid == 0) reset_lists(sm);
+    if (!PRE && tid == 0) reset_lists(sm);
     __syncthreads();
     if (s_abort) break;
     // 3) normals, 4) projection, smoothing and pruning
-    stage2<K, R, NT>(sm, st, th);
+    stage2<K, R, NT, PRE>(sm, st, th);
     __syncthreads();
     float tout[K], aout[K];
     bool aact[K];
@@ -1348,7 +1406,8 @@ __global__ void __launch_bounds__(persist_threads<R>(), MINB) k_iter_persistent(
         act[k] = aact[k];
       }
     }
-    __syncthreads();  // the next gradient step rewrites the tile's shared state
+    if (PRE && tid == 0) reset_lists(sm);  // read above, before stage 3's barrier
+    __syncthreads();  // the next gradient step rewrites the tile's shared state (and lists)
   }
 }
 
@@ -1526,7 +1585,9 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
   // static + dynamic shared memory may exceed the 48 KB default
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
   int bps = 0;
-  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, persist_threads<R>(), zsmem));
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, persist_block<K, R, R == 1 ? 3 : 1>(),
+                                                                    zsmem));
+  int block = persist_block<K, R, R == 1 ? 3 : 1>();
   const uint32_t th = persistent_tile_height<R>(st.rows, st.cols, ctx->num_sms, bps);
   if (th == 0) return SRT3D_EAGAIN;
   const uint32_t tiles_x = (st.cols + kTW - 1) / kTW;
@@ -1537,8 +1598,12 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
       auto fn2 = k_iter_persistent<K, R, 2>;
       SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(zsmem)));
       int bps2 = 0;
-      SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, fn2, persist_threads<R>(), zsmem));
-      if (bps2 >= 2) fn = fn2;
+      SRT3D_CUDA_TRY(ctx,
+                     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps2, fn2, persist_block<K, R, 2>(), zsmem));
+      if (bps2 >= 2) {
+        fn = fn2;
+        block = persist_block<K, R, 2>();
+      }
     }
   }
   if (ntiles * kTileFlagStride > kMaxTileFlags) return SRT3D_EAGAIN;
@@ -1567,7 +1632,7 @@ srt3d_status launch_iter_persistent(srt3d_ctx* ctx, const Stencil& st, const flo
                   &fbase, &skew, &limit, &xt};
   const ProfMark mk = prof_begin(ctx, KID_ITER_ALL, stream);
   const srt3d_status ls = launch_cooperative_chained(ctx, reinterpret_cast<const void*>(fn), dim3(ntiles),
-                                                     dim3(persist_threads<R>()), args, zsmem, stream);
+                                                     dim3(block), args, zsmem, stream);
   prof_end(ctx, KID_ITER_ALL, mk, stream);
   return ls;
   }
