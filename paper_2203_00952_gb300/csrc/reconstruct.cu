@@ -42,6 +42,7 @@ struct Scratch {
   float* xch;  // exchange buffer 0 of the persistent kernel: t, alpha [P][K] f32, active [P][K] u8
   uint8_t* act1;
   float2* hh;
+  float4* part;  // [m][kPrepSlices] partial sums (H, Re, Im) of hhat, slice after slice
   float* misc;
   unsigned* tile_flags;  // [kMaxTileFlags] progress of each tile of the persistent kernel
   // two tagged exchange buffers of the persistent kernel, [2][P][K] x 16 B
@@ -54,6 +55,8 @@ struct Scratch {
 // slow the polls down); frames with more tiles than fit run one launch per
 // iteration.
 constexpr uint32_t kMaxTileFlags = 4096;
+// Slices of tau over which the CTAs of k_prep_part sum hhat.
+constexpr uint32_t kPrepSlices = 8;
 constexpr uint32_t kTileFlagStride = 8;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -63,7 +66,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t scratch_min_bytes(uint32_t P, uint32_t K) {
   const size_t pk = size_t(P) * K;
   return align256(pk * 16) + 2 * align256(pk * sizeof(float)) + align256(pk) + align256(kMaxM * sizeof(float2)) +
-         align256(MISC_COUNT * sizeof(float)) + align256(kMaxTileFlags * sizeof(unsigned));
+         align256(kMaxM * kPrepSlices * sizeof(float4)) + align256(MISC_COUNT * sizeof(float)) +
+         align256(kMaxTileFlags * sizeof(unsigned));
 }
 size_t scratch_xtag_bytes(uint32_t P, uint32_t K) { return align256(2 * size_t(P) * K * 16); }
 
@@ -81,6 +85,8 @@ Scratch carve(void* base, size_t bytes, uint32_t P, uint32_t K) {
   p += align256(pk);
   s.hh = reinterpret_cast<float2*>(p);
   p += align256(kMaxM * sizeof(float2));
+  s.part = reinterpret_cast<float4*>(p);
+  p += align256(kMaxM * kPrepSlices * sizeof(float4));
   s.misc = reinterpret_cast<float*>(p);
   p += align256(MISC_COUNT * sizeof(float));
   s.tile_flags = reinterpret_cast<unsigned*>(p);
@@ -90,50 +96,45 @@ Scratch carve(void* base, size_t bytes, uint32_t P, uint32_t K) {
   return s;
 }
 
-// One block: hhat, H and the step-size bases eta_t * n_max, eta_alpha *
-// n_max; n_max itself is left to the init kernels, which read every pixel's
-// count anyway. Every warp works: harmonic l takes floor(32 / m) warps, each
-// summing h(tau) e^{i w_l tau} over its own slice of tau (stride 32 x warps
-// per harmonic), with the exact table index (l tau) mod T advanced by integer
-// addition; the slices are added in slice order by lane l - 1 of warp 0. The
-// phase table is read through L1 (no shared-memory copy).
+// hhat_l = (1/H) sum_tau h(tau) e^{i w_l tau} (Eq. 4) is summed over
+// kPrepSlices slices of tau, each by a group of kPrepGroup threads (thread t
+// takes tau = lo + t, lo + t + kPrepGroup, ... in order, kPrepUnroll terms
+// per pass with their loads issued together; the group's warps reduce by xor
+// shuffles and are added in warp order); the slices are then added in slice
+// order. The single-frame path runs one group per CTA over many CTAs
+// (k_prep_part, k_prep_final), the batch four groups per frame's CTA
+// (k_prep_batch): the same sums in the same order, so both give the same
+// hhat bit for bit. Phases from the table at the exact index (l tau) mod T.
 constexpr int kPrepUnroll = 8;
-__device__ __forceinline__ void prep_body(const float* __restrict__ h, const uint32_t* __restrict__ n, uint32_t P,
-                                          uint32_t T, uint32_t m, uint32_t K, const float2* __restrict__ table,
-                                          uint32_t entries, int two_level, float2* __restrict__ hh_out,
-                                          float* __restrict__ misc, unsigned* __restrict__ tile_flags,
-                                          uint32_t flag_words) {
-  __shared__ float3 s_part[32];
-  for (uint32_t i = threadIdx.x; i < flag_words; i += blockDim.x) tile_flags[i] = 0u;
-  const bool tl = two_level != 0;
+constexpr uint32_t kPrepGroup = 256;
+constexpr uint32_t kPrepGroupWarps = kPrepGroup / 32;
+
+// This thread's (t in [0, kPrepGroup)) sums of slice sl of harmonic l,
+// reduced over its warp (every lane gets the warp's sums).
+__device__ __forceinline__ float3 prep_slice_warp(const float* __restrict__ h, uint32_t T, uint32_t l, uint32_t sl,
+                                                  const float2* __restrict__ table, bool tl, uint32_t t) {
+  const uint32_t lo = uint32_t(uint64_t(T) * sl / kPrepSlices), hi = uint32_t(uint64_t(T) * (sl + 1u) / kPrepSlices);
   const float invT = 1.0f / float(T);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t wpl = max(nwarps / m, 1u);  // warps per harmonic (m <= 32)
+  uint32_t tau = lo + t;
+  uint32_t k = tau < hi ? mulmod(l, tau, T, invT) : 0u;
+  const uint32_t dk = mulmod(l, kPrepGroup % T, T, invT);
   float hs = 0.f, re = 0.f, im = 0.f;
-  if (warp < wpl * m) {
-    const uint32_t l = warp % m + 1u, slice = warp / m, stride = 32u * wpl;
-    uint32_t tau = slice * 32u + lane;
-    uint32_t k = tau < T ? mulmod(l, tau, T, invT) : 0u;
-    const uint32_t dk = mulmod(l, stride % T, T, invT);
-    // kPrepUnroll terms per pass, their loads issued together (the table and
-    // h come from L2 on first touch); terms past T add exact zeros
-    for (; tau < T; tau += kPrepUnroll * stride) {
-      float hv[kPrepUnroll];
-      float2 e[kPrepUnroll];
+  for (; tau < hi; tau += kPrepUnroll * kPrepGroup) {
+    float hv[kPrepUnroll];
+    float2 e[kPrepUnroll];
 #pragma unroll
-      for (int j = 0; j < kPrepUnroll; ++j) {
-        const uint32_t tj = tau + uint32_t(j) * stride;
-        hv[j] = tj < T ? __ldg(h + tj) : 0.f;
-        e[j] = tj < T ? phase(table, k, tl) : make_float2(0.f, 0.f);
-        k += dk;
-        k -= (k >= T) ? T : 0u;
-      }
+    for (int j = 0; j < kPrepUnroll; ++j) {
+      const uint32_t tj = tau + uint32_t(j) * kPrepGroup;  // terms past the slice add exact zeros
+      hv[j] = tj < hi ? __ldg(h + tj) : 0.f;
+      e[j] = tj < hi ? phase(table, k, tl) : make_float2(0.f, 0.f);
+      k += dk;
+      k -= (k >= T) ? T : 0u;
+    }
 #pragma unroll
-      for (int j = 0; j < kPrepUnroll; ++j) {
-        hs += hv[j];
-        re = fmaf(hv[j], e[j].x, re);
-        im = fmaf(hv[j], e[j].y, im);
-      }
+    for (int j = 0; j < kPrepUnroll; ++j) {
+      hs += hv[j];
+      re = fmaf(hv[j], e[j].x, re);
+      im = fmaf(hv[j], e[j].y, im);
     }
   }
   for (int off = 16; off; off >>= 1) {
@@ -141,16 +142,31 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
     re += __shfl_xor_sync(0xffffffffu, re, off);
     im += __shfl_xor_sync(0xffffffffu, im, off);
   }
-  if (lane == 0) s_part[warp] = make_float3(hs, re, im);
-  __syncthreads();
-  if (warp != 0) return;
-  // lane l - 1 of warp 0: hhat_l from the slices of harmonic l, then the
-  // step-size sums over the harmonics
+  return make_float3(hs, re, im);
+}
+
+// The group's warps' sums added in warp order.
+__device__ __forceinline__ float4 prep_slice_total(const float3* w) {
+  float3 t = w[0];
+  for (uint32_t i = 1; i < kPrepGroupWarps; ++i) {
+    t.x += w[i].x;
+    t.y += w[i].y;
+    t.z += w[i].z;
+  }
+  return make_float4(t.x, t.y, t.z, 0.f);
+}
+
+// Warp 0: hhat from the slices (part[(l - 1) kPrepSlices + slice]), the
+// step-size bases eta_t * n_max, eta_alpha * n_max and the misc scalars
+// (n_max itself is left to the init kernels, which read every count anyway).
+__device__ __forceinline__ void prep_final_warp(const float4* part, uint32_t T, uint32_t m, uint32_t K,
+                                                float2* __restrict__ hh_out, float* __restrict__ misc) {
+  const uint32_t lane = threadIdx.x & 31u;
   float sw = 0.f, sa = 0.f;
   if (lane < m) {
     float H = 0.f, R = 0.f, I = 0.f;
-    for (uint32_t sl = 0; sl < wpl; ++sl) {
-      const float3 v = s_part[sl * m + lane];
+    for (uint32_t sl = 0; sl < kPrepSlices; ++sl) {
+      const float4 v = part[lane * kPrepSlices + sl];
       H += v.x;
       R += v.y;
       I += v.z;
@@ -171,24 +187,54 @@ __device__ __forceinline__ void prep_body(const float* __restrict__ h, const uin
   misc[MISC_ETA_A] = 1.f / (2.f * float(K) * sa);
   misc[MISC_E2] = sa;
   reinterpret_cast<unsigned*>(misc)[MISC_NMAX] = 0u;  // n_max: atomicMax by the init kernels
-  reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;      // grid barrier: arrivals
-  reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;  // (unused)
+  reinterpret_cast<unsigned*>(misc)[MISC_BAR] = 0u;
+  reinterpret_cast<unsigned*>(misc)[MISC_BAR + 1] = 0u;
 }
 
-__global__ void __launch_bounds__(1024) k_prep(const float* __restrict__ h, const uint32_t* __restrict__ n,
-                                               uint32_t P, uint32_t T, uint32_t m, uint32_t K,
-                                               const float2* __restrict__ table, uint32_t entries, int two_level,
-                                               float2* __restrict__ hh_out, float* __restrict__ misc,
-                                               unsigned* __restrict__ tile_flags) {
-  prep_body(h, n, P, T, m, K, table, entries, two_level, hh_out, misc, tile_flags, kMaxTileFlags);
+// Single frame: CTA (slice, l - 1) writes part[(l - 1) kPrepSlices + slice].
+__global__ void __launch_bounds__(kPrepGroup) k_prep_part(const float* __restrict__ h, uint32_t T,
+                                                          const float2* __restrict__ table, int two_level,
+                                                          float4* __restrict__ part) {
+  __shared__ float3 s_w[kPrepGroupWarps];
+  const uint32_t sl = blockIdx.x, l = blockIdx.y + 1u;
+  const float3 v = prep_slice_warp(h, T, l, sl, table, two_level != 0, threadIdx.x);
+  if ((threadIdx.x & 31u) == 0) s_w[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) part[(l - 1u) * kPrepSlices + sl] = prep_slice_total(s_w);
 }
 
-// Batched: one block per frame of the batch (each zeroes its tiles' flags).
+// Single frame: hhat and the scalars from the slices; zeroes the progress flags.
+__global__ void __launch_bounds__(1024) k_prep_final(const float4* __restrict__ part, uint32_t T, uint32_t m,
+                                                     uint32_t K, float2* __restrict__ hh_out,
+                                                     float* __restrict__ misc, unsigned* __restrict__ tile_flags) {
+  for (uint32_t i = threadIdx.x; i < kMaxTileFlags; i += blockDim.x) tile_flags[i] = 0u;
+  if (threadIdx.x < 32) prep_final_warp(part, T, m, K, hh_out, misc);
+}
+
+// Batched: one block per frame of the batch, four slice groups at a time
+// (each zeroes its tiles' flags).
 __global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restrict__ frames, uint32_t K,
                                                      unsigned* __restrict__ tile_flags) {
+  constexpr uint32_t kGroups = 1024 / kPrepGroup;
+  __shared__ float3 s_w[kGroups][kPrepGroupWarps];
+  __shared__ float4 s_part[kMaxM * kPrepSlices];
   const BatchFrame& f = frames[blockIdx.x];
-  prep_body(f.h, f.n, f.P, f.T, f.m, K, f.table, f.tab_entries, f.two_level, f.hh, f.misc,
-            tile_flags + size_t(f.tile0) * kTileFlagStride, f.tiles_x * f.tiles_y * kTileFlagStride);
+  unsigned* fl = tile_flags + size_t(f.tile0) * kTileFlagStride;
+  const uint32_t flag_words = f.tiles_x * f.tiles_y * kTileFlagStride;
+  for (uint32_t i = threadIdx.x; i < flag_words; i += blockDim.x) fl[i] = 0u;
+  const uint32_t g = threadIdx.x / kPrepGroup, t = threadIdx.x % kPrepGroup;
+  const uint32_t pairs = f.m * kPrepSlices;
+  for (uint32_t base = 0; base < pairs; base += kGroups) {  // uniform trip count (barriers inside)
+    const uint32_t pr = base + g;
+    if (pr < pairs) {
+      const float3 v = prep_slice_warp(f.h, f.T, pr / kPrepSlices + 1u, pr % kPrepSlices, f.table, f.two_level != 0, t);
+      if ((t & 31u) == 0) s_w[g][t >> 5] = v;
+    }
+    __syncthreads();
+    if (pr < pairs && t == 0) s_part[pr] = prep_slice_total(s_w[g]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) prep_final_warp(s_part, f.T, f.m, K, f.hh, f.misc);
 }
 
 // Sketched gradient step (Jacobi) of one pixel's K points: reads the state
@@ -1647,8 +1693,8 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
   const int tl = tab.two_level ? 1 : 0;
   {
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
-    k_prep<<<1, 1024, 0, stream>>>(h, n, P, T, m, K, tab.dev, tab.entries, tl, sc.hh, sc.misc,
-                                          sc.tile_flags);
+    k_prep_part<<<dim3(kPrepSlices, m), kPrepGroup, 0, stream>>>(h, T, tab.dev, tl, sc.part);
+    k_prep_final<<<1, 1024, 0, stream>>>(sc.part, T, m, K, sc.hh, sc.misc, sc.tile_flags);
     prof_end(ctx, KID_PREP, mk, stream);
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
