@@ -390,7 +390,8 @@ srt3d_status srt3d_plan(uint32_t rows, uint32_t cols, uint32_t T, uint32_t m, ui
  * launch count. srt3d_profile_enable(ctx, 1) clears the totals and starts
  * recording, 0 stops. srt3d_profile_read() waits for the recorded events and
  * returns the totals of kernel `kernel` (an index < srt3d_kernel_count());
- * srt3d_kernel_name() names it. */
+ * srt3d_kernel_name() names it. An entry can span consecutive launches of
+ * one stage ("prep" of a single frame is two kernels, both counted). */
 srt3d_status srt3d_profile_enable(srt3d_ctx* ctx, int enable);
 srt3d_status srt3d_profile_read(srt3d_ctx* ctx, uint32_t kernel, double* total_ms, uint64_t* launches);
 uint32_t srt3d_kernel_count(void);

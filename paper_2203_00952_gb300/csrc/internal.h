@@ -98,6 +98,7 @@ struct Profiler {
   struct Pending {
     uint32_t kid;
     cudaEvent_t a, b;
+    uint32_t kernels;  // kernel launches between the two events
   };
   std::vector<Pending> pending;
   double total_ms[KID_COUNT] = {};
@@ -231,7 +232,7 @@ struct ProfMark {
   cudaEvent_t a = nullptr, b = nullptr;
 };
 ProfMark prof_begin(srt3d_ctx* ctx, uint32_t kid, cudaStream_t stream);
-void prof_end(srt3d_ctx* ctx, uint32_t kid, const ProfMark& mk, cudaStream_t stream);
+void prof_end(srt3d_ctx* ctx, uint32_t kid, const ProfMark& mk, cudaStream_t stream, uint32_t kernels = 1);
 
 }  // namespace srt3d
 

@@ -30,11 +30,11 @@ ProfMark prof_begin(srt3d_ctx* ctx, uint32_t kid, cudaStream_t stream) {
   return mk;
 }
 
-void prof_end(srt3d_ctx* ctx, uint32_t kid, const ProfMark& mk, cudaStream_t stream) {
+void prof_end(srt3d_ctx* ctx, uint32_t kid, const ProfMark& mk, cudaStream_t stream, uint32_t kernels) {
   if (!mk.a || !mk.b) return;
   cudaEventRecord(mk.b, stream);
   std::lock_guard<std::mutex> lock(ctx->prof.mu);
-  ctx->prof.pending.push_back({kid, mk.a, mk.b});
+  ctx->prof.pending.push_back({kid, mk.a, mk.b, kernels});
 }
 
 static void drain(Profiler& pf) {
@@ -42,7 +42,7 @@ static void drain(Profiler& pf) {
     float ms = 0.f;
     if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       pf.total_ms[p.kid] += ms;
-      pf.launches[p.kid] += 1;
+      pf.launches[p.kid] += p.kernels;
     }
     pf.pool.push_back(p.a);
     pf.pool.push_back(p.b);

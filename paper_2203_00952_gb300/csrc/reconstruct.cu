@@ -1695,7 +1695,7 @@ srt3d_status run(srt3d_ctx* ctx, const float2* z, const uint32_t* n, uint32_t ro
     const ProfMark mk = prof_begin(ctx, KID_PREP, stream);
     k_prep_part<<<dim3(kPrepSlices, m), kPrepGroup, 0, stream>>>(h, T, tab.dev, tl, sc.part);
     k_prep_final<<<1, 1024, 0, stream>>>(sc.part, T, m, K, sc.hh, sc.misc, sc.tile_flags);
-    prof_end(ctx, KID_PREP, mk, stream);
+    prof_end(ctx, KID_PREP, mk, stream, 2);
   }
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   if (prm.init_mode == SRT3D_INIT_MATCHED) {
