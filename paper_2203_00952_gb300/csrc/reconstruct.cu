@@ -243,14 +243,22 @@ __global__ void __launch_bounds__(1024) k_prep_batch(const BatchFrame* __restric
 // residual products of both points in packed FP32 pairs: per harmonic, q_k =
 // hhat_l e^{i w_l t_k}, psi = sum_k a_k q_k, r = z_l - psi, the alpha gradient
 // sums r . q_k, the depth gradient sums w_l Im(conj(q_k) r) (times a_k at the
-// end), and e^{i w_l t_k} advances by one complex rotation.
+// end), and e^{i w_l t_k} advances by one complex rotation. e^{i w_1 t_k}
+// comes from the special-function unit: for t in [0, T) the phase in
+// revolutions t / T - 1/2 lies in [-1/2, 1/2), where the SFU's sine and
+// cosine are accurate to ~4e-7 absolute, and e^{i w_1 t} is the negated pair
+// (a shorter dependent chain than the full-precision sincospi).
 __device__ __forceinline__ void grad_pixel_pair(const float2* __restrict__ zp, uint32_t cnt, uint32_t T, uint32_t m,
                                                 const float2* s_hh, float eta_t, float eta_a, float (&t)[2],
                                                 float (&a)[2], const bool (&act)[2]) {
-  const float Tf = float(T);
+  const float Tf = float(T), invT = 1.f / Tf;
   float s0, c0, s1, c1;
-  sincospif(2.f * t[0] / Tf, &s0, &c0);
-  sincospif(2.f * t[1] / Tf, &s1, &c1);
+  __sincosf(6.283185307179586f * fmaf(t[0], invT, -0.5f), &s0, &c0);
+  __sincosf(6.283185307179586f * fmaf(t[1], invT, -0.5f), &s1, &c1);
+  s0 = -s0;
+  c0 = -c0;
+  s1 = -s1;
+  c1 = -c1;
   const float2 e1x = make_float2(c0, c1), e1y = make_float2(s0, s1), ne1y = make_float2(-s0, -s1);
   float2 Ex = e1x, Ey = e1y;
   const float aa0 = act[0] ? a[0] : 0.f, aa1 = act[1] ? a[1] : 0.f;
