@@ -570,8 +570,9 @@ __device__ __forceinline__ float4 plane_normal(int cnt, float Sw, float Sx, floa
   if (cnt >= 3 && det > 1e-6f * Sw * Sw * Sw) {
     const float db = Sw * (Sxz * Syy - Sxy * Syz) - Sz * (Sx * Syy - Sxy * Sy) + Sy * (Sx * Syz - Sxz * Sy);
     const float dcf = Sw * (Sxx * Syz - Sxz * Sxy) - Sx * (Sx * Syz - Sxz * Sy) + Sz * (Sx * Sxy - Sxx * Sy);
-    const float b = db / det, c = dcf / det;
-    const float inv = 1.f / sqrtf(b * b + c * c + 1.f);
+    const float idet = 1.f / det;
+    const float b = db * idet, c = dcf * idet;
+    const float inv = rsqrtf(b * b + c * c + 1.f);
     return make_float4(-b * inv, -c * inv, inv, 0.f);
   }
   return make_float4(0.f, 0.f, 1.f, 0.f);
@@ -581,13 +582,14 @@ __device__ __forceinline__ float4 plane_normal(int cnt, float Sw, float Sx, floa
 // (Guennebaud & Gross 2007, with normals); tq when the fit is rejected.
 __device__ __forceinline__ float sphere_depth(const Stencil& st, float tq, int cnt, float Sw, float Spx, float Spy,
                                               float Spz, float Snx, float Sny, float Snz, float Spn, float Spp) {
-  const float den = Spp - (Spx * Spx + Spy * Spy + Spz * Spz) / Sw;
+  const float iw = 1.f / Sw;  // (one division; the sums are scaled by its reciprocal)
+  const float den = Spp - (Spx * Spx + Spy * Spy + Spz * Spz) * iw;
   if (cnt >= 3 && den > 0.f) {
-    const float u4 = 0.5f * (Spn - (Spx * Snx + Spy * Sny + Spz * Snz) / Sw) / den;
-    const float ux = (Snx - 2.f * u4 * Spx) / Sw;
-    const float uy = (Sny - 2.f * u4 * Spy) / Sw;
-    const float uz = (Snz - 2.f * u4 * Spz) / Sw;
-    const float u0 = -(ux * Spx + uy * Spy + uz * Spz + u4 * Spp) / Sw;
+    const float u4 = 0.5f * (Spn - (Spx * Snx + Spy * Sny + Spz * Snz) * iw) / den;
+    const float ux = (Snx - 2.f * u4 * Spx) * iw;
+    const float uy = (Sny - 2.f * u4 * Spy) * iw;
+    const float uz = (Snz - 2.f * u4 * Spz) * iw;
+    const float u0 = -(ux * Spx + uy * Spy + uz * Spz + u4 * Spp) * iw;
     const float disc = uz * uz - 4.f * u4 * u0;
     if (disc >= 0.f) {
       const float sq = sqrtf(disc);
