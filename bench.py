@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # current kernels on this workload, from the committed ncu captures named
 # beside them; a kernel changed since its capture must be taken out of here
 NCU_TRAFFIC = {
-    "iter_all": (None, "profiles/k_iter_persistent_256x256_T4096_m10_K2_it30.md (kernel changed since the capture)"),
+    "iter_all": (7.777536e6, "profiles/k_iter_persistent_256x256_T4096_m10_K2_it30.md"),
     "sketch_stream": (136.272896e6, "profiles/k_sketch_stream_256x256_T4096_m10.md"),
 }
 SM_COUNT = 152
