@@ -977,8 +977,9 @@ def gpu_arm(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step(st, sd, od, zz):
-        B.srt3d_sketch_stream(ctx, sd, od, T, m, 0, S, n, st)
-        B.srt3d_finalize(ctx, S, n, m, zz, st)
+        # a frame sketched in one call: the sketch stores z = S / n itself
+        # (accumulate = 2), the values srt3d_finalize would give
+        B.srt3d_sketch_stream(ctx, sd, od, T, m, 2, zz, n, st)
         B.srt3d_reconstruct(ctx, zz, n, spec.rows, spec.cols, T, m, h, params, depth, alpha, active, alpha0, st)
 
     for _ in range(max(args.warmup, 3)):

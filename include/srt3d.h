@@ -157,11 +157,16 @@ srt3d_status srt3d_hist_from_stream(srt3d_ctx* ctx, const uint16_t* stamps, cons
  *   every 8 harmonics when m > 10 (at most 3.5e-6 per term for m <= 10,
  *   2.3e-6 with restarts). For T > 8192 the table is two-level and harmonics
  *   come from complex rotation by e_1, resynchronised at the exact integer
- *   phase every 16 harmonics. The sums are FP32.
+ *   phase every 16 harmonics; for m <= 2, half of each 16-byte word's
+ *   photons take e_1 from the special-function unit instead (phase reduced to
+ *   [-pi, pi); same per-term bound). The sums are FP32.
  *   stamps, offsets, num_stamps, T as for srt3d_hist_from_stream
  *   m        1..32
  *   accumulate  0: overwrite S and n;  1: add into S and n (online update of
- *            Sec. 2: a frame's photons may arrive in chunks)
+ *            Sec. 2: a frame's photons may arrive in chunks);  2: overwrite
+ *            with the normalised sketch z = S / n (0 where n = 0) and n, the
+ *            values srt3d_finalize would give bit for bit: a frame sketched
+ *            in one call needs no separate finalize
  *   S        device, float [num_pixels][m][2] (re, im interleaved)
  *   n        device, uint32 [num_pixels]
  * Stamps >= T are skipped and latch SRT3D_ERANGE. */

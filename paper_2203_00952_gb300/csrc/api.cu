@@ -208,7 +208,9 @@ srt3d_status srt3d_sketch_stream(srt3d_ctx* ctx, const uint16_t* stamps, const u
   if (num_stamps >= (1ull << 32) - 16) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32 - 16");
   if (reinterpret_cast<uintptr_t>(S) % 8) return set_error(ctx, SRT3D_EINVAL, "S must be 8-byte aligned");
   if (num_pixels == 0) return SRT3D_OK;
-  return launch_sketch_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, m, accumulate ? 1 : 0,
+  // 0 overwrite, 1 accumulate (any other nonzero value too), 2 store z = S / n
+  const int mode = accumulate == 2 ? 2 : (accumulate ? 1 : 0);
+  return launch_sketch_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, m, mode,
                               reinterpret_cast<float2*>(S), n, static_cast<cudaStream_t>(stream));
 }
 

@@ -111,6 +111,28 @@ def test_sketch_online_chunks_accumulate(ctx):
     assert sketch_err(S, n, S_ref, n_ref) <= TOL
 
 
+@pytest.mark.parametrize("T,m", [(4096, 1), (4096, 10), (1024, 32), (65536, 7)])
+def test_sketch_normalised_mode_equals_finalize(ctx, T, m):
+    """accumulate = 2 stores z = S / n directly: bit for bit what
+    srt3d_finalize gives after an overwriting sketch (empty pixels: 0)."""
+    rng = np.random.default_rng(70 + m)
+    per = [rng.integers(0, T, size=int(c)) for c in rng.integers(0, 1500, size=50)]
+    per[3] = per[3][:0]
+    st, off = csr(per)
+    P = len(per)
+    S = torch.empty(P, m, 2, device="cuda")
+    n = torch.empty(P, dtype=torch.int32, device="cuda")
+    z = torch.empty(P, m, 2, device="cuda")
+    B.srt3d_sketch_stream(ctx, dev_stamps(st), dev_offsets(off), T, m, 0, S, n)
+    B.srt3d_finalize(ctx, S, n, m, z)
+    z2 = torch.full((P, m, 2), float("nan"), device="cuda")
+    n2 = torch.zeros(P, dtype=torch.int32, device="cuda")
+    B.srt3d_sketch_stream(ctx, dev_stamps(st), dev_offsets(off), T, m, 2, z2, n2)
+    B.srt3d_sync(ctx)
+    assert torch.equal(n, n2)
+    assert torch.equal(z, z2)
+
+
 def test_sketch_full_256x256_sampled(ctx):
     # The benchmark's workload at full size; the oracle recomputes a sample of pixels.
     spec = synth.frame_256x256()
