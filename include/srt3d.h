@@ -290,9 +290,12 @@ srt3d_status srt3d_process_batch(srt3d_ctx* ctx, const srt3d_frame* frames, uint
  *   carried in kernel parameters (the same values srt3d_reconstruct uses, so
  *   the results are bit for bit those of srt3d_reconstruct).
  *   All calls share the array and it keeps the last call's contents (every
- *   word is rewritten before use, nothing needs clearing): calls that overlap
+ *   word is rewritten before use, and the iterations' exchange words, which
+ *   must start at zero, are cleared by each call itself): calls that overlap
  *   on the GPU (different streams or contexts of the same device) race and
- *   must be serialised by the caller.
+ *   must be serialised by the caller. Frames of up to about 290 000 points
+ *   (rows * cols * k_max) also fit the iterations' tagged exchange buffers;
+ *   larger ones exchange state through progress flags (same results, slower).
  *   Profiling (srt3d_profile_enable) must be off: it creates CUDA events. */
 srt3d_status srt3d_reconstruct_noalloc(srt3d_ctx* ctx, const float* z, const uint32_t* n, uint32_t rows,
                                        uint32_t cols, uint32_t T, uint32_t m, const float* h,
