@@ -312,13 +312,13 @@ __device__ __forceinline__ void grad_pixel(const float2* __restrict__ zp, uint32
     grad_pixel_pair(zp, cnt, T, m, s_hh, eta_t, eta_a, t, a, act);
     return;
   }
-  const float Tf = float(T);
+  const float Tf = float(T), invT = 1.f / Tf;
   float2 e1[K], E[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    float sn, cs;
-    sincospif(2.f * t[k] / Tf, &sn, &cs);
-    e1[k] = make_float2(cs, sn);
+    float sn, cs;  // e^{i w_1 t} from the SFU as in grad_pixel_pair
+    __sincosf(6.283185307179586f * fmaf(t[k], invT, -0.5f), &sn, &cs);
+    e1[k] = make_float2(-cs, -sn);
     E[k] = e1[k];
   }
   float gt[K], ga[K];
