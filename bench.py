@@ -318,12 +318,15 @@ def hist_section(B, ctx, dev, steps, flush, rows=512):
 
 # ----------------------------------------------------------------- stream via tensor cores
 def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
-    """Sketch of the 256x256 stamp stream two ways, at m = 10 and m = 32:
-    the CUDA-core stream kernel (srt3d_sketch_stream) and the composed
+    """Sketch of the 256x256 stamp stream three ways, at m = 10 and m = 32:
+    the CUDA-core stream kernel (srt3d_sketch_stream), the composed
     tensor-core route (device histogram, then the split-FP16 tcgen05 sketch;
-    srt3d_sketch_stream_tc). Device time per call (CUDA events, L2 evicted
-    between calls) and the error of the second against the first. Also the
-    CUDA-core kernel at m = 1 and 4 against the HBM roofline."""
+    srt3d_sketch_stream_tc) and the fused one (stamps sorted by stage, each
+    stage's histogram built in shared memory; srt3d_sketch_stream_tc_fused).
+    Device time per call (CUDA events, L2 evicted between calls), the error of
+    the second against the first and whether the third equals the second bit
+    for bit. Also the CUDA-core kernel at m = 1 and 4 against the HBM
+    roofline."""
     import numpy as np
     import torch
 
@@ -355,10 +358,25 @@ def stream_tc_section(B, ctx, dev, stamps, offsets, fr, spec, steps, flush):
                                                        stream))
         nn = torch.clamp(n1.to(torch.float32), min=1.0)[:, None]
         err = float(((S2 - S1).norm(dim=-1) / nn).max().item())
-        out[f"m{m}"] = {"cuda_cores_ms": ms_cc, "tensor_cores_ms": ms_tc,
+        S3 = torch.empty(P, m, 2, device=dev)
+        n3 = torch.empty(P, dtype=torch.int32, device=dev)
+        ms_fu = timed(lambda: B.srt3d_sketch_stream_tc_fused(ctx, stamps, offsets, T, m, B.SRT3D_FP16_SPLIT, S3,
+                                                             n3, stream))
+        # the fused route's two kernels, timed apart (profiler events)
+        B.srt3d_profile_enable(ctx, True)
+        for i in range(3):
+            flush.fill_(float(i))
+            B.srt3d_sketch_stream_tc_fused(ctx, stamps, offsets, T, m, B.SRT3D_FP16_SPLIT, S3, n3, stream)
+        torch.cuda.synchronize(dev)
+        prof = B.profile_totals(ctx)
+        B.srt3d_profile_enable(ctx, False)
+        fused_split = {k: v[0] / max(v[1], 1) for k, v in prof.items() if k in ("bucket_stream", "sketch_stream_tc")}
+        out[f"m{m}"] = {"cuda_cores_ms": ms_cc, "tensor_cores_ms": ms_tc, "fused_tensor_cores_ms": ms_fu,
                         "cuda_cores_photons_per_s": N / (ms_cc / 1e3), "tensor_cores_photons_per_s": N / (ms_tc / 1e3),
-                        "counts_equal": bool(torch.equal(n1, n2)), "max_diff_normalised": err}
-        del S1, S2, n1, n2
+                        "fused_tensor_cores_photons_per_s": N / (ms_fu / 1e3), "fused_kernels_ms": fused_split,
+                        "counts_equal": bool(torch.equal(n1, n2)), "max_diff_normalised": err,
+                        "fused_equals_composed": bool(torch.equal(S2, S3) and torch.equal(n2, n3))}
+        del S1, S2, S3, n1, n2, n3
     # few harmonics: where the CUDA-core kernel's arithmetic falls below its
     # 2 bytes per photon, it is bound by HBM (algorithmic bytes: the stamps,
     # the offsets, the sums and the counts)

@@ -202,6 +202,25 @@ srt3d_status srt3d_sketch_stream_tc(srt3d_ctx* ctx, const uint16_t* stamps, cons
                                     uint64_t num_stamps, uint32_t num_pixels, uint32_t T, uint32_t m,
                                     int precision, float* S, uint32_t* n, void* stream);
 
+/* srt3d_sketch_stream_tc without the histogram in HBM (Sec. 2, Eqs. 2-3): the
+ * stamps of every tile of 128 pixels are first counting-sorted by bin / 64
+ * into 2-byte entries, then the tensor-core kernel builds each 128 x 64-bin
+ * stage of the histogram in shared memory from its entries (shared-memory
+ * atomics), converts it in place and multiplies it by the Fourier stage. HBM
+ * traffic: the stamps read twice and their entries written and read once,
+ * against the num_pixels x T histogram written and read by
+ * srt3d_sketch_stream_tc. Same arguments, precisions and results: S and n are
+ * bit-identical to srt3d_sketch_stream_tc's (the same integer counts enter
+ * the same products), except that a pixel with more than 65535 stamps
+ * counts only its first 65535 (reported by srt3d_sync as a count out of
+ * range). Stamps >= T are skipped, offsets out of order or past num_stamps
+ * leave the pixel empty; both are reported by srt3d_sync. The sorted entries
+ * (2 bytes per stamp) and the bucket starts live in a context-owned device
+ * buffer: calls on one context must not overlap on different streams. */
+srt3d_status srt3d_sketch_stream_tc_fused(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                          uint64_t num_stamps, uint32_t num_pixels, uint32_t T, uint32_t m,
+                                          int precision, float* S, uint32_t* n, void* stream);
+
 /* Normalise sketch states (Sec. 2, Eq. 3): z = S / n, and z = 0 where n = 0.
  *   S  device float [P][m][2];  n device uint32 [P];  z device float [P][m][2]
  *   (z may alias S). */

@@ -118,6 +118,8 @@ _SIGS = {
     "srt3d_sketch_stream": (_i32, [_vp, _vp, _vp, _u64, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
     "srt3d_sketch_hist": (_i32, [_vp, _vp, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
     "srt3d_sketch_stream_tc": (_i32, [_vp, _vp, _vp, ctypes.c_uint64, _u32, _u32, _u32, _i32, _vp, _vp, _vp]),
+    "srt3d_sketch_stream_tc_fused": (_i32, [_vp, _vp, _vp, ctypes.c_uint64, _u32, _u32, _u32, _i32, _vp, _vp,
+                                             _vp]),
     "srt3d_finalize": (_i32, [_vp, _vp, _vp, _u32, _u32, _vp, _vp]),
     "srt3d_reconstruct": (_i32, [_vp, _vp, _vp, _u32, _u32, _u32, _u32, _vp, ctypes.POINTER(srt3d_params), _vp,
                                  _vp, _vp, _vp, _vp]),
@@ -223,6 +225,17 @@ def srt3d_sketch_stream_tc(ctx, stamps, offsets, T, m, precision, S, n, stream=N
                                       stamps.numel(), P, int(T), int(m), int(precision), _dev(S, torch.float32, "S"),
                                       _dev(n, torch.int32, "n"), _stream(stream))
     return _check(ctx, st, "srt3d_sketch_stream_tc")
+
+
+def srt3d_sketch_stream_tc_fused(ctx, stamps, offsets, T, m, precision, S, n, stream=None):
+    import torch
+
+    P = offsets.numel() - 1
+    st = lib().srt3d_sketch_stream_tc_fused(ctx, _dev(stamps, torch.int16, "stamps"),
+                                            _dev(offsets, torch.int32, "offsets"), stamps.numel(), P, int(T), int(m),
+                                            int(precision), _dev(S, torch.float32, "S"), _dev(n, torch.int32, "n"),
+                                            _stream(stream))
+    return _check(ctx, st, "srt3d_sketch_stream_tc_fused")
 
 
 def srt3d_sketch_hist(ctx, hist, T, m, precision, S, n, stream=None):

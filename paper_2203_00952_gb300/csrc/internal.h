@@ -88,6 +88,8 @@ enum KernelId : uint32_t {
   KID_ALPHA0,
   KID_BATCH,
   KID_BIRTH,
+  KID_BUCKET_STREAM,
+  KID_SKETCH_STREAM_TC,
   KID_COUNT
 };
 

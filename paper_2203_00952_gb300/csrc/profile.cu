@@ -6,7 +6,7 @@ namespace srt3d {
 static const char* kKernelNames[KID_COUNT] = {
     "sketch_stream", "finalize", "hist_from_stream", "sketch_hist_fp32", "sketch_hist_tc",
     "prep",          "init",     "grad",             "iter",             "iter_all",         "alpha0",
-    "batch_graph",   "birth"};
+    "batch_graph",   "birth",    "bucket_stream",    "sketch_stream_tc"};
 
 static cudaEvent_t take_event(Profiler& pf) {
   if (!pf.pool.empty()) {

@@ -15,6 +15,10 @@ namespace srt3d {
 
 srt3d_status launch_sketch_hist_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_t T, uint32_t m,
                                    int precision, float2* S, uint32_t* n, cudaStream_t stream);
+size_t stream_tc_fused_scratch_bytes(uint64_t num_stamps, uint32_t P, uint32_t T);
+srt3d_status launch_sketch_stream_tc_fused(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                           uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int precision,
+                                           float2* S, uint32_t* n, void* scratch, cudaStream_t stream);
 
 namespace {
 
@@ -181,4 +185,33 @@ extern "C" srt3d_status srt3d_sketch_stream_tc(srt3d_ctx* ctx, const uint16_t* s
   st = launch_hist_from_stream(ctx, stamps, offsets, num_stamps, num_pixels, T, hist, s);
   if (st != SRT3D_OK) return st;
   return launch_sketch_hist_tc(ctx, hist, num_pixels, T, m, precision, reinterpret_cast<float2*>(S), n, s);
+}
+
+// The same stream sketch with the histogram built in shared memory, one
+// tensor-core stage (64 bins of 128 pixels) at a time, from the stamps
+// counting-sorted by stage (k_bucket_stream). Only the stamps and their 2-byte
+// sorted entries cross HBM, not the num_pixels x T histogram.
+extern "C" srt3d_status srt3d_sketch_stream_tc_fused(srt3d_ctx* ctx, const uint16_t* stamps,
+                                                     const uint32_t* offsets, uint64_t num_stamps,
+                                                     uint32_t num_pixels, uint32_t T, uint32_t m, int precision,
+                                                     float* S, uint32_t* n, void* stream) {
+  if (!ctx) return SRT3D_EINVAL;
+  if (!offsets || !S || !n || (num_stamps && !stamps)) return set_error(ctx, SRT3D_EINVAL, "NULL pointer");
+  if (T < 64 || T > 65536 || T % 64 != 0) return set_error(ctx, SRT3D_EINVAL, "T must be a multiple of 64 in [64, 65536]");
+  if (m < 1 || m > 32) return set_error(ctx, SRT3D_EINVAL, "m must be in [1, 32]");
+  if (precision != SRT3D_FP16_SPLIT && precision != SRT3D_BF16)
+    return set_error(ctx, SRT3D_EINVAL, "precision must be SRT3D_FP16_SPLIT or SRT3D_BF16");
+  if (num_stamps >= (1ull << 32)) return set_error(ctx, SRT3D_EINVAL, "num_stamps must be < 2^32");
+  if (num_pixels >= (1u << 31)) return set_error(ctx, SRT3D_EINVAL, "num_pixels must be < 2^31");
+  if (reinterpret_cast<uintptr_t>(S) % 8) return set_error(ctx, SRT3D_EINVAL, "S must be 8-byte aligned");
+  if (num_pixels == 0) return SRT3D_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  srt3d_status st;
+  {
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    st = grow(ctx, &ctx->hist_scratch, stream_tc_fused_scratch_bytes(num_stamps, num_pixels, T));
+  }
+  if (st != SRT3D_OK) return st;
+  return launch_sketch_stream_tc_fused(ctx, stamps, offsets, num_stamps, num_pixels, T, m, precision,
+                                       reinterpret_cast<float2*>(S), n, ctx->hist_scratch.ptr, s);
 }

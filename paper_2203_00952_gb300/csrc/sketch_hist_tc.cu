@@ -23,6 +23,16 @@
 // Every mbarrier wait is bounded: on timeout the kernel latches an error flag,
 // lets every role leave its loop, waits (bounded) for its own TMA copies and
 // MMAs, frees TMEM and returns.
+//
+// Fused stream route (FUSED = true): no histogram in HBM. k_bucket_stream
+// first counting-sorts each tile's in-range stamps by bin / 64, the stage that
+// consumes them, into 2-byte entries (row << 6) | (bin & 63). The producer
+// then loads only F^T; the converter warps become builders: per stage they
+// zero the A slot, count the stage's entries into it with shared-memory
+// atomics on the packed u16 bins (the slot's swizzled layout, i.e. the tile
+// the TMA would have brought), and convert it in place as above. The builders
+// agree on every early exit through a barrier reduction, so none waits at a
+// named barrier that another has left.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -157,6 +167,8 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t M, uint32_t N, uint32
 }
 
 constexpr int kMaxStages = 8;
+constexpr uint32_t kBuildRegs = 8;                 // fused builders: entries per thread per batch
+constexpr uint32_t kBuildBatch = 256u * kBuildRegs;  // entries per batch of the 256 builders
 
 template <int PREC>
 struct TcCfg {
@@ -165,11 +177,27 @@ struct TcCfg {
 
 // ------------------------------------------------------------------ the kernel
 
-template <int PREC>
+// Barrier 1 over the 256 converter threads: true on every thread when v is
+// true on any (barrier.red also orders their shared-memory accesses).
+__device__ __forceinline__ bool conv_bar_any(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n barrier.cta.red.or.pred q, 1, 256, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"(uint32_t(v))
+      : "memory");
+  return r != 0u;
+}
+
+__device__ __forceinline__ void conv_bar() { asm volatile("barrier.cta.sync 1, 256;" ::: "memory"); }
+
+template <int PREC, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_hist_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapF,
                      uint32_t P, uint32_t T, uint32_t m, uint32_t N2, uint32_t ncols_alloc, uint32_t ST,
-                     float2* __restrict__ S, uint32_t* __restrict__ n, uint32_t* __restrict__ gflags) {
+                     float2* __restrict__ S, uint32_t* __restrict__ n, uint32_t* __restrict__ gflags,
+                     const uint16_t* __restrict__ ent, const uint32_t* __restrict__ tinfo) {
   using Cfg = TcCfg<PREC>;
   constexpr bool kSplit = Cfg::kSplit;
   const uint32_t N = kSplit ? 2u * N2 : N2;  // MMA N (rows of F^T per stage)
@@ -231,8 +259,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (uint32_t tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
           if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, abort_flag, gflags)) break;
-          mbar_arrive_expect_tx(smem_u32(&full[s]), kABytes + b_bytes);
-          tma_load_2d(smem_u32(sA(s)), &mapY, smem_u32(&full[s]), int(kt * kTileK), int(tile * kTileM));
+          if (FUSED) {
+            mbar_arrive_expect_tx(smem_u32(&full[s]), b_bytes);
+          } else {
+            mbar_arrive_expect_tx(smem_u32(&full[s]), kABytes + b_bytes);
+            tma_load_2d(smem_u32(sA(s)), &mapY, smem_u32(&full[s]), int(kt * kTileK), int(tile * kTileM));
+          }
           tma_load_2d(smem_u32(sB(s)), &mapF, smem_u32(&full[s]), int(kt * kTileK), 0);
           if (++s == ST) {
             s = 0;
@@ -318,12 +350,77 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t it = 0, s = 0, ph = 0;
     uint32_t ps = 0, pph = 0;  // slot and phase parity of stage it - 1
     bool ok = true;
+    bool fail = false;  // FUSED: a wait of this thread gave up; the next vote ends every builder's loop
     for (uint32_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       uint32_t cnt = 0;
+      const uint32_t* ti = FUSED ? tinfo + size_t(tile) * (KT + 2u) : nullptr;
+      const uint32_t ebase = FUSED ? __ldg(ti) : 0u;
+      // stage kt's entries are ent[ebase + start[kt], ebase + start[kt + 1]);
+      // the first kBuildBatch of them are loaded one stage ahead, into pe. A
+      // thread takes kBuildRegs consecutive entries (a pixel's entries sit
+      // together in a bucket, so a warp's lanes then meet less on one word)
+      uint32_t e_lo = 0u, e_hi = 0u;
+      uint32_t pe[kBuildRegs];
+      if (FUSED) {
+        e_lo = ebase + __ldg(ti + 1);
+        e_hi = ebase + __ldg(ti + 2);
+#pragma unroll
+        for (uint32_t k = 0; k < kBuildRegs; ++k) {
+          const uint32_t i = e_lo + ct * kBuildRegs + k;
+          pe[k] = i < e_hi ? uint32_t(__ldg(ent + i)) : 0xffffffffu;
+        }
+      }
       for (uint32_t kt = 0; kt < KT; ++kt, ++it) {
-        if (!(ok = mbar_wait(smem_u32(&full[s]), ph, abort_flag, gflags))) break;
         uint8_t* ra = sA(s) + row * 128u;
         uint8_t* ra2 = a2_slot + row * 128u;
+        if (FUSED) {
+          // full[s] completes once F^T landed, i.e. after the MMAs that last
+          // read slot s completed: the slot is free to rebuild
+          const bool go = mbar_wait(smem_u32(&full[s]), ph, abort_flag, gflags);
+          if (go) {
+#pragma unroll
+            for (uint32_t c = 0; c < 4; ++c)
+              *reinterpret_cast<uint4*>(ra + (((c0 + c) ^ sw) << 4)) = make_uint4(0u, 0u, 0u, 0u);
+          }
+          if (conv_bar_any(fail || !go)) {
+            ok = false;
+            break;
+          }
+          // the stage's entries: bins [64 kt, 64 kt + 64) of the tile's rows
+          const uint32_t n_hi = kt + 1u < KT ? ebase + __ldg(ti + 3u + kt) : e_hi;  // next stage's end
+          uint8_t* a = sA(s);
+          auto count = [&](uint32_t e) {
+            const uint32_t r = (e >> 6) & 127u, b = e & 63u;  // r < 128 by construction
+            // the u32 word of (r, b) in the 128-byte swizzled row, and the half of it
+            const uint32_t off = r * 128u + ((((b >> 3) ^ (r & 7u)) << 4) | ((b & 6u) << 1));
+            atomicAdd(reinterpret_cast<uint32_t*>(a + off), 1u << ((b & 1u) << 4));
+          };
+#pragma unroll
+          for (uint32_t k = 0; k < kBuildRegs; ++k)
+            if (pe[k] != 0xffffffffu) count(pe[k]);
+          for (uint32_t i0 = e_lo + kBuildBatch + ct * kBuildRegs; i0 < e_hi; i0 += kBuildBatch) {
+            uint32_t e[kBuildRegs];
+#pragma unroll
+            for (uint32_t k = 0; k < kBuildRegs; ++k) {
+              const uint32_t i = i0 + k;
+              e[k] = i < e_hi ? uint32_t(__ldg(ent + i)) : 0xffffffffu;
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < kBuildRegs; ++k)
+              if (e[k] != 0xffffffffu) count(e[k]);
+          }
+          // the next stage's first batch, in flight while this stage converts
+          e_lo = e_hi;
+          e_hi = n_hi;
+#pragma unroll
+          for (uint32_t k = 0; k < kBuildRegs; ++k) {
+            const uint32_t i = e_lo + ct * kBuildRegs + k;
+            pe[k] = i < e_hi ? uint32_t(__ldg(ent + i)) : 0xffffffffu;
+          }
+          conv_bar();
+        } else {
+          if (!(ok = mbar_wait(smem_u32(&full[s]), ph, abort_flag, gflags))) break;
+        }
         uint32_t w[16];
 #pragma unroll
         for (uint32_t c = 0; c < 4; ++c) {
@@ -394,7 +491,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         // at most one phase behind it: this thread converted stage it - 1,
         // whose data the producer loaded only after the previous phase
         // completed. So the parity wait cannot alias an older phase.
-        if (rewrite_a2 && it > 0u && !(ok = mbar_wait(smem_u32(&empty[ps]), pph, abort_flag, gflags))) break;
+        if (rewrite_a2 && it > 0u && !mbar_wait(smem_u32(&empty[ps]), pph, abort_flag, gflags)) {
+          if (!FUSED) {
+            ok = false;
+            break;
+          }
+          // no early exit between the builders' barriers: skip this stage's
+          // writes and leave at the next vote (or at the end of the loops)
+          fail = true;
+          ps = s;
+          pph = ph;
+          if (++s == ST) {
+            s = 0;
+            ph ^= 1u;
+          }
+          continue;
+        }
 #pragma unroll
         for (uint32_t c = 0; c < 4; ++c) {
           const uint32_t off = ((c0 + c) ^ sw) << 4;
@@ -417,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) break;
       const uint32_t p = tile * kTileM + row;
-      if (p < P) atomicAdd(n + p, cnt);  // two halves per row; n was zeroed before the launch
+      if (!FUSED && p < P) atomicAdd(n + p, cnt);  // two halves per row; n was zeroed before the launch
     }
   } else if (warp >= 12) {
     // ---------------------------------------------------------------- epilogue
@@ -461,6 +573,239 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     tmem_dealloc(tmem_base, ncols_alloc);
   }
+}
+
+// ------------------------------------------------------------------ stamp buckets (fused route)
+
+// k_bucket_stream: for every tile of kTileM pixels, the tile's in-range stamps
+// counting-sorted by bin / kTileK (the tensor-core stage that consumes them)
+// and each pixel's count n of them,
+// each as a 2-byte entry (row << 6) | (bin & 63). tinfo[tile] holds
+// {base, start[0], ..., start[KT]}: stage kt's entries are
+// ent[base + start[kt], base + start[kt + 1]). The bins' counts are what the
+// histogram of Eq. 2 holds, so the order inside a bucket does not matter.
+//
+// Pass 1 reads the tile's stamps and counts each bucket (shared-memory
+// atomics); a block scan turns the counts into the bucket starts and one
+// global atomic claims the tile's range of ent. Pass 2 re-reads the stamps in
+// chunks of kBucketChunk, sorts each chunk in shared memory by bucket, and
+// writes every bucket's run of the chunk contiguously after the bucket's
+// previous runs, so the global stores are coalesced. The photons of a pixel
+// crowd into one or two buckets (the surface's return), so every bucket's
+// counters are replicated R times, the replica chosen by the stamp's index:
+// at most 32 / R lanes of a warp meet on one counter. A pixel counts at most
+// its first 65535 stamps (more raise FLAG_COUNT_RANGE: every bin count then
+// fits the 16-bit counters of the builders); stamps >= T are skipped and raise
+// FLAG_STAMP_RANGE, and offsets out of order or past num_stamps raise
+// FLAG_OFFSETS and leave the pixel empty.
+constexpr uint32_t kBucketThreads = 256;
+constexpr uint32_t kBucketChunk = 4096;  // six CTAs per SM: every tile of a 256 x 256 frame at once
+constexpr uint32_t kBucketUnroll = 8;                   // stamp loads in flight per lane
+constexpr uint32_t kBucketHead = 128 + 128 + 132 + 16;  // u32 words before the bucket arrays
+
+__host__ __device__ constexpr uint32_t bucket_rep_log2(uint32_t KT) {
+  return KT <= 256u ? 3u : KT <= 512u ? 2u : 1u;  // 2048 replicated counters at most
+}
+__host__ __device__ constexpr size_t bucket_al256(size_t b) { return (b + 255) & ~size_t(255); }
+__host__ __device__ constexpr size_t bucket_ent_bytes(uint64_t num_stamps) {
+  return bucket_al256(size_t(num_stamps > 0 ? num_stamps : 1) * sizeof(uint16_t));
+}
+__host__ __device__ constexpr size_t bucket_tinfo_bytes(uint64_t ntiles, uint32_t T) {
+  return bucket_al256(size_t(ntiles) * (T / kTileK + 2u) * sizeof(uint32_t));
+}
+__host__ __device__ constexpr size_t bucket_smem_bytes(uint32_t KT) {
+  return (kBucketHead + 4u * (size_t(KT) << bucket_rep_log2(KT)) + KT + 4u) * sizeof(uint32_t) +
+         3u * kBucketChunk * sizeof(uint16_t);
+}
+
+// Exclusive prefix sum of in[0, K) into out (may alias in) over the whole
+// block; returns the total. s_warp holds 8 words. Every thread must call it.
+__device__ uint32_t bucket_scan(const uint32_t* in, uint32_t* out, uint32_t K, uint32_t* s_warp) {
+  const uint32_t q = (K + kBucketThreads - 1) / kBucketThreads;
+  const uint32_t a = threadIdx.x * q, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t sum = 0;
+  for (uint32_t j = 0; j < q; ++j)
+    if (a + j < K) sum += in[a + j];
+  uint32_t x = sum;
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31u) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t run = x - sum, total = 0;
+  for (uint32_t w = 0; w < kBucketThreads / 32u; ++w) {
+    const uint32_t v = s_warp[w];
+    if (w < warp) run += v;
+    total += v;
+  }
+  for (uint32_t j = 0; j < q; ++j)
+    if (a + j < K) {
+      const uint32_t v = in[a + j];
+      out[a + j] = run;
+      run += v;
+    }
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_stream(const uint16_t* __restrict__ stamps,
+                                                                   const uint32_t* __restrict__ offsets,
+                                                                   uint32_t num_stamps, uint32_t P, uint32_t T,
+                                                                   uint16_t* __restrict__ ent, uint32_t cap,
+                                                                   uint32_t* __restrict__ tinfo,
+                                                                   uint32_t* __restrict__ claim,
+                                                                   uint32_t* __restrict__ n,
+                                                                   uint32_t* __restrict__ flags) {
+  extern __shared__ __align__(16) uint32_t smb[];
+  const uint32_t KT = T / kTileK;
+  const uint32_t rl = bucket_rep_log2(KT), R = 1u << rl, KR = KT << rl;
+  uint32_t* s_beg = smb;          // [128] first stamp of each row
+  uint32_t* s_len = s_beg + 128;  // [128] stamps of each row counted (at most 65535)
+  uint32_t* s_R = s_len + 128;    // [132] exclusive prefix of s_len
+  uint32_t* s_misc = s_R + 132;   // [16] scan partials, the tile's base and whether it fits
+  uint32_t* cntr = smb + kBucketHead;  // [KR] tile counts per (bucket, replica), then their starts
+  uint32_t* lc = cntr + KR;            // [KR] the chunk's counts per (bucket, replica)
+  uint32_t* lo = lc + KR;              // [KR + 1] exclusive prefix of lc, and the chunk's total
+  uint32_t* lcur = lo + KR + 4;        // [KR] scatter cursors
+  uint32_t* gcur = lcur + KR;          // [KT] each bucket's next position in ent (from base)
+  uint16_t* xe = reinterpret_cast<uint16_t*>(gcur + KT);  // [chunk] entry of each staged stamp
+  uint16_t* xb = xe + kBucketChunk;                       // [chunk] its (bucket, replica), 0xffff out of range
+  uint16_t* xo = xb + kBucketChunk;                       // [chunk] entries sorted by bucket
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t kWarps = kBucketThreads / 32u;
+  const uint32_t ntiles = (P + kTileM - 1) / kTileM;
+  bool bad = false, bad_off = false, over = false;
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    __syncthreads();  // the previous tile's shared arrays are no longer read
+    if (tid < kTileM) {
+      const uint32_t p = tile * kTileM + tid;
+      uint32_t b = 0, len = 0;
+      if (p < P) {
+        const uint32_t s = __ldg(offsets + p), e = __ldg(offsets + p + 1);
+        if (e < s || e > num_stamps) {
+          bad_off = true;
+        } else {
+          b = s;
+          len = e - s;
+          if (len > 65535u) {
+            over = true;
+            len = 65535u;
+          }
+        }
+      }
+      s_beg[tid] = b;
+      s_len[tid] = len;
+    }
+    for (uint32_t k = tid; k < KR; k += kBucketThreads) {
+      cntr[k] = 0u;
+      lc[k] = 0u;
+    }
+    __syncthreads();
+    const uint32_t L = bucket_scan(s_len, s_R, kTileM, s_misc);
+    // pass 1: counts per (bucket, replica = lane mod R), kBucketUnroll loads in flight per lane
+    const uint32_t rep1 = lane & (R - 1u);
+    for (uint32_t r = warp; r < kTileM; r += kWarps) {
+      const uint32_t b = s_beg[r], len = s_len[r];
+      uint32_t inr = 0;  // the row's in-range stamps: n of Eq. 3
+      for (uint32_t j0 = 0; j0 < len; j0 += 32u * kBucketUnroll) {
+        uint32_t x[kBucketUnroll];
+#pragma unroll
+        for (uint32_t k = 0; k < kBucketUnroll; ++k) {
+          const uint32_t j = j0 + lane + 32u * k;
+          x[k] = j < len ? uint32_t(__ldg(stamps + b + j)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < kBucketUnroll; ++k) {
+          if (x[k] == 0xffffffffu) continue;
+          if (x[k] < T) {
+            atomicAdd(&cntr[((x[k] / kTileK) << rl) | rep1], 1u);
+            ++inr;
+          } else {
+            bad = true;
+          }
+        }
+      }
+      inr = __reduce_add_sync(0xffffffffu, inr);
+      const uint32_t p = tile * kTileM + r;
+      if (lane == 0 && p < P) n[p] = inr;
+    }
+    __syncthreads();
+    const uint32_t V = bucket_scan(cntr, cntr, KR, s_misc);  // cntr[k R] = start of bucket k
+    if (tid == 0) {
+      const uint32_t base = atomicAdd(claim, V);
+      const bool fits = uint64_t(base) + V <= cap;  // only overlapping pixel ranges can overrun
+      if (!fits) bad_off = true;
+      s_misc[8] = fits ? base : 0u;
+      s_misc[9] = fits ? 1u : 0u;
+    }
+    __syncthreads();
+    const uint32_t base = s_misc[8];
+    const bool fits = s_misc[9] != 0u;
+    uint32_t* ti = tinfo + size_t(tile) * (KT + 2u);
+    if (tid == 0) ti[0] = base;
+    for (uint32_t k = tid; k <= KT; k += kBucketThreads) {
+      const uint32_t st = k < KT ? cntr[k << rl] : V;
+      ti[1 + k] = fits ? st : 0u;
+      if (k < KT) gcur[k] = st;
+    }
+    if (!fits) continue;
+    // pass 2: chunks of the tile's stamps, sorted by bucket in shared memory;
+    // the replica of the stamp at chunk position i is i mod R
+    for (uint32_t c0 = 0; c0 < L; c0 += kBucketChunk) {
+      const uint32_t nc = min(kBucketChunk, L - c0);
+      for (uint32_t r = warp; r < kTileM; r += kWarps) {
+        const uint32_t R0 = s_R[r], len = s_len[r];
+        if (R0 + len <= c0 || R0 >= c0 + nc) continue;
+        const uint32_t j0 = c0 > R0 ? c0 - R0 : 0u, j1 = min(len, c0 + nc - R0);
+        const uint32_t b = s_beg[r];
+        for (uint32_t jj = j0; jj < j1; jj += 32u * kBucketUnroll) {
+          uint32_t x[kBucketUnroll];
+#pragma unroll
+          for (uint32_t k = 0; k < kBucketUnroll; ++k) {
+            const uint32_t j = jj + lane + 32u * k;
+            x[k] = j < j1 ? uint32_t(__ldg(stamps + b + j)) : 0xffffffffu;
+          }
+#pragma unroll
+          for (uint32_t k = 0; k < kBucketUnroll; ++k) {
+            if (x[k] == 0xffffffffu) continue;
+            const uint32_t i = R0 + jj + lane + 32u * k - c0;
+            if (x[k] < T) {
+              const uint32_t kr = ((x[k] / kTileK) << rl) | (i & (R - 1u));
+              xe[i] = uint16_t((r << 6) | (x[k] & (kTileK - 1)));
+              xb[i] = uint16_t(kr);
+              atomicAdd(&lc[kr], 1u);
+            } else {
+              xb[i] = 0xffffu;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t nv = bucket_scan(lc, lo, KR, s_misc);
+      for (uint32_t k = tid; k < KR; k += kBucketThreads) lcur[k] = lo[k];
+      if (tid == 0) lo[KR] = nv;
+      __syncthreads();
+      for (uint32_t i = tid; i < nc; i += kBucketThreads) {
+        const uint32_t kr = xb[i];
+        if (kr != 0xffffu) xo[atomicAdd(&lcur[kr], 1u)] = xe[i];
+      }
+      __syncthreads();
+      // bucket k's run of the chunk: xo[lo[k R], lo[(k + 1) R]) (its replicas are adjacent)
+      for (uint32_t k = warp; k < KT; k += kWarps) {
+        const uint32_t src = lo[k << rl], c = lo[(k + 1u) << rl] - src, dst = base + gcur[k];
+        for (uint32_t j = lane; j < c; j += 32u) ent[dst + j] = xo[src + j];
+        __syncwarp();
+        if (lane == 0) gcur[k] += c;
+      }
+      for (uint32_t k = tid; k < KR; k += kBucketThreads) lc[k] = 0u;
+      __syncthreads();
+    }
+  }
+  if (bad_off) atomicOr(flags, FLAG_OFFSETS);
+  if (bad) atomicOr(flags, FLAG_STAMP_RANGE);
+  if (over) atomicOr(flags, FLAG_COUNT_RANGE);
 }
 
 // ------------------------------------------------------------------ host side
@@ -539,9 +884,11 @@ srt3d_status get_fourier_operand(srt3d_ctx* ctx, uint32_t T, uint32_t m, int pre
   return SRT3D_OK;
 }
 
-template <int PREC>
+// FUSED: hist is unused; ent / tinfo are k_bucket_stream's output.
+template <int PREC, bool FUSED>
 srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_t T, uint32_t m, float2* S,
-                       uint32_t* n, cudaStream_t stream) {
+                       uint32_t* n, cudaStream_t stream, const uint16_t* ent = nullptr,
+                       const uint32_t* tinfo = nullptr) {
   using Cfg = TcCfg<PREC>;
   const uint32_t N2 = ((2 * m + 15) / 16) * 16;
   const uint32_t N = Cfg::kSplit ? 2 * N2 : N2;
@@ -551,7 +898,7 @@ srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_
   srt3d_status st = get_fourier_operand(ctx, T, m, PREC, N2, &F);
   if (st != SRT3D_OK) return st;
   CUtensorMap mapY, mapF;
-  if (!encode_map(&mapY, hist, P, T, kTileM) || !encode_map(&mapF, F, N, T, N))
+  if (!encode_map(&mapF, F, N, T, N) || (FUSED ? (mapY = mapF, false) : !encode_map(&mapY, hist, P, T, kTileM)))
     return set_error(ctx, SRT3D_ECUDA, "cuTensorMapEncodeTiled failed");
   // stages: as many as fit (at most kMaxStages) beside the A2 slot, the
   // 1024-byte alignment pad and the barrier block
@@ -561,14 +908,15 @@ srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_
   const uint32_t ST = uint32_t(std::min<size_t>(kMaxStages, fit));
   if (ST < 2) return set_error(ctx, SRT3D_EINVAL, "tensor-core tile does not fit shared memory");
   const size_t smem = fixed + ST * stage_bytes;
-  auto kfn = k_sketch_hist_tc<PREC>;
+  auto kfn = k_sketch_hist_tc<PREC, FUSED>;
   SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const uint32_t ntiles = (P + kTileM - 1) / kTileM;
   const uint32_t grid = std::min<uint32_t>(ntiles, uint32_t(ctx->num_sms));
-  SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(n, 0, size_t(P) * sizeof(uint32_t), stream));
-  const ProfMark mk = prof_begin(ctx, KID_SKETCH_HIST_TC, stream);
-  kfn<<<grid, kThreads, smem, stream>>>(mapY, mapF, P, T, m, N2, ncols_alloc, ST, S, n, ctx->d_flags);
-  prof_end(ctx, KID_SKETCH_HIST_TC, mk, stream);
+  if (!FUSED) SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(n, 0, size_t(P) * sizeof(uint32_t), stream));
+  const int kid = FUSED ? KID_SKETCH_STREAM_TC : KID_SKETCH_HIST_TC;
+  const ProfMark mk = prof_begin(ctx, kid, stream);
+  kfn<<<grid, kThreads, smem, stream>>>(mapY, mapF, P, T, m, N2, ncols_alloc, ST, S, n, ctx->d_flags, ent, tinfo);
+  prof_end(ctx, kid, mk, stream);
   SRT3D_CUDA_TRY(ctx, cudaGetLastError());
   return SRT3D_OK;
 }
@@ -577,8 +925,39 @@ srt3d_status launch_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_
 
 srt3d_status launch_sketch_hist_tc(srt3d_ctx* ctx, const uint16_t* hist, uint32_t P, uint32_t T, uint32_t m,
                                    int precision, float2* S, uint32_t* n, cudaStream_t stream) {
-  if (precision == SRT3D_FP16_SPLIT) return launch_tc<SRT3D_FP16_SPLIT>(ctx, hist, P, T, m, S, n, stream);
-  return launch_tc<SRT3D_BF16>(ctx, hist, P, T, m, S, n, stream);
+  if (precision == SRT3D_FP16_SPLIT) return launch_tc<SRT3D_FP16_SPLIT, false>(ctx, hist, P, T, m, S, n, stream);
+  return launch_tc<SRT3D_BF16, false>(ctx, hist, P, T, m, S, n, stream);
+}
+
+size_t stream_tc_fused_scratch_bytes(uint64_t num_stamps, uint32_t P, uint32_t T) {
+  const uint64_t ntiles = (uint64_t(P) + kTileM - 1) / kTileM;
+  return bucket_ent_bytes(num_stamps) + bucket_tinfo_bytes(ntiles, T) + 256;
+}
+
+srt3d_status launch_sketch_stream_tc_fused(srt3d_ctx* ctx, const uint16_t* stamps, const uint32_t* offsets,
+                                           uint64_t num_stamps, uint32_t P, uint32_t T, uint32_t m, int precision,
+                                           float2* S, uint32_t* n, void* scratch, cudaStream_t stream) {
+  const uint32_t ntiles = (P + kTileM - 1) / kTileM;
+  uint8_t* sc = static_cast<uint8_t*>(scratch);
+  uint16_t* ent = reinterpret_cast<uint16_t*>(sc);
+  uint32_t* tinfo = reinterpret_cast<uint32_t*>(sc + bucket_ent_bytes(num_stamps));
+  uint32_t* claim = reinterpret_cast<uint32_t*>(sc + bucket_ent_bytes(num_stamps) + bucket_tinfo_bytes(ntiles, T));
+  const uint32_t KT = T / kTileK;
+  const size_t smem = bucket_smem_bytes(KT);
+  SRT3D_CUDA_TRY(ctx, cudaFuncSetAttribute(k_bucket_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int bps = 0;
+  SRT3D_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_bucket_stream, kBucketThreads, smem));
+  if (bps < 1) bps = 1;
+  const uint32_t grid = std::min<uint32_t>(ntiles, uint32_t(ctx->num_sms) * uint32_t(bps));
+  SRT3D_CUDA_TRY(ctx, cudaMemsetAsync(claim, 0, sizeof(uint32_t), stream));
+  const ProfMark mk = prof_begin(ctx, KID_BUCKET_STREAM, stream);
+  k_bucket_stream<<<grid, kBucketThreads, smem, stream>>>(stamps, offsets, uint32_t(num_stamps), P, T, ent,
+                                                          uint32_t(num_stamps), tinfo, claim, n, ctx->d_flags);
+  prof_end(ctx, KID_BUCKET_STREAM, mk, stream);
+  SRT3D_CUDA_TRY(ctx, cudaGetLastError());
+  if (precision == SRT3D_FP16_SPLIT)
+    return launch_tc<SRT3D_FP16_SPLIT, true>(ctx, nullptr, P, T, m, S, n, stream, ent, tinfo);
+  return launch_tc<SRT3D_BF16, true>(ctx, nullptr, P, T, m, S, n, stream, ent, tinfo);
 }
 
 }  // namespace srt3d

@@ -161,3 +161,115 @@ def test_stream_sketch_through_tensor_cores(ctx, T, m, sizes):
     assert sketch_err(S, n, S_ref, n_ref) <= 1e-5
     with pytest.raises(B.SRT3DError):
         B.srt3d_sketch_stream_tc(ctx, sd, off, 100, m, B.SRT3D_FP16_SPLIT, S, n)
+
+
+# ----------------------------------------------------------------- fused stream route
+def both_stream_routes(ctx, stamps, offsets, T, m, precision=B.SRT3D_FP16_SPLIT, check=True):
+    """S, n of srt3d_sketch_stream_tc (histogram through HBM) and of
+    srt3d_sketch_stream_tc_fused (histogram stages built in shared memory);
+    outputs start as NaN / -1 so that nothing unwritten passes."""
+    P = len(offsets) - 1
+    sd = dev_stamps(stamps) if stamps.size else torch.zeros(8, dtype=torch.int16, device="cuda")[:0]
+    off = dev_offsets(offsets)
+    out, status = [], []
+    for fn in (B.srt3d_sketch_stream_tc, B.srt3d_sketch_stream_tc_fused):
+        S = torch.full((P, m, 2), float("nan"), device="cuda")
+        n = torch.full((P,), -1, dtype=torch.int32, device="cuda")
+        fn(ctx, sd, off, T, m, precision, S, n)
+        status.append(B.srt3d_sync(ctx, check=check))
+        out.append((S, n))
+    return out, status
+
+
+def _per_pixel(rng, T, sizes):
+    return [rng.integers(0, T, size=c) for c in sizes]
+
+
+@pytest.mark.parametrize("T,m,sizes", [
+    (4096, 10, [1000, 0, 37, 5000, 3]),
+    (1024, 32, [300, 301, 1, 0]),
+    (64, 3, [0, 12, 7]),
+    (4096, 10, "ragged300"),     # three tiles, the last one 44 pixels
+    (2048, 16, "chunks"),        # a tile of 45 K stamps: several sort chunks, one pixel spanning three
+    (65536, 4, "ragged130"),     # 1024 stages per tile
+    (4096, 1, "empty"),          # no stamps at all
+])
+def test_fused_stream_route_equals_composed_and_oracle(ctx, T, m, sizes):
+    # the same integer bin counts enter the same tensor-core products, so S
+    # and n equal the composed route's bit for bit; both equal the oracle's
+    # stream sketch within the split-FP16 bound (Sec. 2, Eq. 3)
+    rng = np.random.default_rng(T + m + 7)
+    if sizes == "ragged300":
+        per = _per_pixel(rng, T, rng.integers(0, 400, size=300))
+    elif sizes == "chunks":
+        per = _per_pixel(rng, T, [200] * 127 + [20000])
+    elif sizes == "ragged130":
+        per = _per_pixel(rng, T, rng.integers(0, 2000, size=130))
+    elif sizes == "empty":
+        per = [np.zeros(0, np.int64)] * 5
+    else:
+        per = _per_pixel(rng, T, sizes)
+    stamps, offsets = csr(per)
+    ((S1, n1), (S2, n2)), _ = both_stream_routes(ctx, stamps, offsets, T, m)
+    assert torch.equal(n1, n2)
+    assert torch.equal(S1, S2)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, T, m)
+    assert np.array_equal(counts(n2), n_ref)
+    assert sketch_err(S2, n2, S_ref, n_ref) <= 1e-5
+
+
+def test_fused_stream_route_big_bin_counts(ctx):
+    # bins above 2048 counts take the exact split A = y & ~31, A2 = y & 31
+    T, m = 1024, 12
+    rng = np.random.default_rng(3)
+    per = [np.full(3000, 17), np.full(2049, 0), rng.integers(0, T, 500),
+           np.concatenate([np.full(4100, 1023), rng.integers(0, T, 100)])] + _per_pixel(rng, T, [50] * 200)
+    stamps, offsets = csr(per)
+    ((S1, n1), (S2, n2)), _ = both_stream_routes(ctx, stamps, offsets, T, m)
+    assert torch.equal(n1, n2) and torch.equal(S1, S2)
+    S_ref, n_ref = oracle.sketch_stream(stamps, offsets, T, m)
+    assert sketch_err(S2, n2, S_ref, n_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("most", [1500, 60])
+def test_fused_stream_route_bf16_equals_composed(ctx, most):
+    # dense pixels: stages above 256 entries count in u16 and convert; sparse
+    # ones add in BF16 directly
+    T, m = 4096, 10
+    rng = np.random.default_rng(11 + most)
+    per = _per_pixel(rng, T, rng.integers(0, most, size=257))
+    stamps, offsets = csr(per)
+    ((S1, n1), (S2, n2)), _ = both_stream_routes(ctx, stamps, offsets, T, m, B.SRT3D_BF16)
+    assert torch.equal(n1, n2) and torch.equal(S1, S2)
+
+
+def test_fused_stream_route_error_cases(ctx):
+    T, m = 256, 4
+    rng = np.random.default_rng(5)
+    # a stamp >= T is skipped by both routes and reported
+    per = _per_pixel(rng, T, [100, 30, 7])
+    per[1] = np.concatenate([per[1], [T, T + 5]])
+    stamps, offsets = csr(per)
+    ((S1, n1), (S2, n2)), st = both_stream_routes(ctx, stamps, offsets, T, m, check=False)
+    assert st == [B.SRT3D_ERANGE, B.SRT3D_ERANGE]
+    assert torch.equal(n1, n2) and torch.equal(S1, S2)
+    # more than 65535 stamps in a pixel: the fused route counts the first
+    # 65535 (the composed route saturates each bin instead); both report it
+    per = [rng.integers(0, T, 70000), rng.integers(0, T, 10)]
+    stamps, offsets = csr(per)
+    (_, (S2, n2)), st = both_stream_routes(ctx, stamps, offsets, T, m, check=False)
+    assert st[1] == B.SRT3D_ERANGE
+    cut, cut_off = csr([per[0][:65535], per[1]])
+    S_ref, n_ref = oracle.sketch_stream(cut, cut_off, T, m)
+    assert np.array_equal(counts(n2), n_ref)
+    assert sketch_err(S2, n2, S_ref, n_ref) <= 1e-5
+    # decreasing offsets: the pixel is left empty and reported
+    stamps = np.arange(10, dtype=np.uint16)
+    offsets = np.array([0, 6, 4, 10], dtype=np.uint32)
+    (_, (S2, n2)), st = both_stream_routes(ctx, stamps, offsets, 64, m, check=False)
+    assert st[1] == B.SRT3D_EOFFSETS
+    assert counts(n2)[1] == 0
+    with pytest.raises(B.SRT3DError):
+        B.srt3d_sketch_stream_tc_fused(ctx, dev_stamps(stamps), dev_offsets(offsets), 100, m, B.SRT3D_FP16_SPLIT,
+                                       torch.zeros(3, m, 2, device="cuda"),
+                                       torch.zeros(3, dtype=torch.int32, device="cuda"))
