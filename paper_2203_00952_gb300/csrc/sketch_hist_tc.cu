@@ -192,6 +192,10 @@ __device__ __forceinline__ bool conv_bar_any(bool v) {
 
 __device__ __forceinline__ void conv_bar() { asm volatile("barrier.cta.sync 1, 256;" ::: "memory"); }
 
+__device__ __forceinline__ void red_shared_add(uint32_t saddr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+
 template <int PREC, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1)
     k_sketch_hist_tc(const __grid_constant__ CUtensorMap mapY, const __grid_constant__ CUtensorMap mapF,
@@ -393,7 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t r = (e >> 6) & 127u, b = e & 63u;  // r < 128 by construction
             // the u32 word of (r, b) in the 128-byte swizzled row, and the half of it
             const uint32_t off = r * 128u + ((((b >> 3) ^ (r & 7u)) << 4) | ((b & 6u) << 1));
-            atomicAdd(reinterpret_cast<uint32_t*>(a + off), 1u << ((b & 1u) << 4));
+            // by shared-window address: the slot pointer is generic, and a
+            // generic atomic would take the slow path
+            red_shared_add(smem_u32(a + off), 1u << ((b & 1u) << 4));
           };
 #pragma unroll
           for (uint32_t k = 0; k < kBuildRegs; ++k)
@@ -599,12 +605,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 // FLAG_STAMP_RANGE, and offsets out of order or past num_stamps raise
 // FLAG_OFFSETS and leave the pixel empty.
 constexpr uint32_t kBucketThreads = 256;
-constexpr uint32_t kBucketChunk = 4096;  // six CTAs per SM: every tile of a 256 x 256 frame at once
+constexpr uint32_t kBucketChunk = 8192;
 constexpr uint32_t kBucketUnroll = 8;                   // stamp loads in flight per lane
 constexpr uint32_t kBucketHead = 128 + 128 + 132 + 16;  // u32 words before the bucket arrays
 
 __host__ __device__ constexpr uint32_t bucket_rep_log2(uint32_t KT) {
-  return KT <= 256u ? 3u : KT <= 512u ? 2u : 1u;  // 2048 replicated counters at most
+  // four replicas up to T = 32768 (four CTAs per SM at T = 4096: every tile
+  // of a 256 x 256 frame in one round), two above
+  return KT <= 512u ? 2u : 1u;
 }
 __host__ __device__ constexpr size_t bucket_al256(size_t b) { return (b + 255) & ~size_t(255); }
 __host__ __device__ constexpr size_t bucket_ent_bytes(uint64_t num_stamps) {
