@@ -101,6 +101,8 @@ def test_null_context_rejected(lib):
     assert lib.srt3d_sketch_stream(None, None, None, 0, 0, 16, 4, 0, None, None, None) == binding.SRT3D_EINVAL
     assert lib.srt3d_reconstruct(None, None, None, 1, 1, 16, 4, None, None, None, None, None, None,
                                  None) == binding.SRT3D_EINVAL
+    for fn in (lib.srt3d_sketch_stream_tc, lib.srt3d_sketch_stream_tc_fused):
+        assert fn(None, None, None, 0, 1, 64, 4, binding.SRT3D_FP16_SPLIT, None, None, None) == binding.SRT3D_EINVAL
 
 
 def test_plan_info_layout():
