@@ -26,13 +26,14 @@
 //
 // Fused stream route (FUSED = true): no histogram in HBM. k_bucket_stream
 // first counting-sorts each tile's in-range stamps by bin / 64, the stage that
-// consumes them, into 2-byte entries (row << 6) | (bin & 63). The producer
-// then loads only F^T; the converter warps become builders: per stage they
-// zero the A slot, count the stage's entries into it with shared-memory
-// atomics on the packed u16 bins (the slot's swizzled layout, i.e. the tile
-// the TMA would have brought), and convert it in place as above. The builders
-// agree on every early exit through a barrier reduction, so none waits at a
-// named barrier that another has left.
+// consumes them, into 2-byte entries (row << 6) | (bin & 63), and writes n.
+// The producer then loads only F^T; the converter warps become builders: per
+// stage they zero the A slot, add the stage's entries into it by shared-memory
+// reductions on the packed u16 bins (the slot's swizzled layout, i.e. the
+// tile the TMA would have brought), and convert it in place as above; the next
+// stage's first entries are loaded while the current one converts. The
+// builders agree on every early exit through a barrier reduction, so none
+// waits at a named barrier that another has left.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
